@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle to facts other than itself.
+
+Each ``check_*`` states a fact fixed by the paper or by plain mathematics and
+checks the oracle against it: a hand-derived worked example (tests/golden),
+brute force through a different formula (Euclidean distance, Section 2.2),
+closed forms (K = 1, N = K, disjoint supports, duplicate means), Lloyd
+invariants (objective never decreases, unit means), the paper's claim that
+IVF (Algorithm 3) keeps the Lloyd solution, and its multiplication count
+(Eq. 15).  ``test_planted_mistakes_are_caught`` plants plausible mistakes in
+the oracle (on the CPU) and requires that some check fails for each.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle.inverted_file as ivf
+import oracle.spherical_kmeans as sk
+from paper_2002_09094_gb300 import datagen as dg
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "worked_examples.json")
+
+
+def tiny_corpus(seed, n_docs=60, n_terms=40, mean_len=6.0, zipf_s=0.8):
+    spec = dg.CorpusSpec(n_docs=n_docs, n_terms=n_terms, length_kind="poisson", length_mean=mean_len,
+                         length_lo=2, length_hi=12, zipf_s=zipf_s, seed=seed)
+    return dg.make_corpus(spec)
+
+
+def dense_rows(corpus):
+    rows = []
+    for i in range(corpus.n_docs):
+        x = [0.0] * corpus.n_terms
+        for h in range(int(corpus.row_ptr[i]), int(corpus.row_ptr[i + 1])):
+            x[int(corpus.term[h])] = float(corpus.val[h])
+        rows.append(x)
+    return rows
+
+
+# ---------------------------------------------------------------- checks
+
+
+def check_golden():
+    spec = json.load(open(GOLDEN))
+    for ex in spec["examples"]:
+        c = dg.corpus_from_rows(ex["rows"], ex["n_terms"])
+        m0 = sk.initial_means(c, ex["init_doc_ids"])
+        its = sk.iterate(c, m0, max_iter=len(ex["iterations"]) + 2, empty_policy=ex["empty_policy"])
+        tol = ex["tolerance"]
+        assert len(its) == len(ex["iterations"]), ex["name"]
+        for it, exp in zip(its, ex["iterations"]):
+            assert it.assign.tolist() == exp["assign"], ex["name"]
+            assert np.allclose(it.best, exp["best"], rtol=0, atol=tol), ex["name"]
+            assert np.allclose(it.gap, exp["gap"], rtol=0, atol=tol), ex["name"]
+            assert abs(it.objective - exp["objective"]) <= 4 * tol, ex["name"]
+            if "n_changed" in exp:
+                assert it.n_changed == exp["n_changed"]
+            if "sum_norm" in exp:
+                assert np.allclose(it.sum_norm, exp["sum_norm"], rtol=0, atol=tol)
+            if "means_after" in exp:
+                for j, (t, v) in enumerate(exp["means_after"]):
+                    mt, mv = it.means_after.row(j)
+                    assert mt.tolist() == t, (ex["name"], j)
+                    assert np.allclose(mv, v, rtol=0, atol=tol), (ex["name"], j)
+
+
+def check_euclidean_brute_force(seed=11):
+    """argmax_j x.mu_j = argmin_j ||x - mu_j||^2 for unit means (Section 2.2),
+    with every distance and mean computed densely in plain Python."""
+    c = tiny_corpus(seed)
+    k = 7
+    ids = dg.init_doc_ids(c.n_docs, k, seed)
+    X = dense_rows(c)
+    mus = []
+    for d in ids:
+        nrm = math.sqrt(sum(v * v for v in X[d]))
+        mus.append([v / nrm for v in X[d]])
+    rho = sk.similarities(c, sk.initial_means(c, ids))
+    a, best, gap = sk.assign_from_similarities(rho)
+    checked = 0
+    for i, x in enumerate(X):
+        xx = sum(v * v for v in x)
+        dist = [sum((xv - mv) ** 2 for xv, mv in zip(x, mu)) for mu in mus]
+        for j in range(k):  # ||x - mu||^2 = ||x||^2 - 2 x.mu + 1
+            assert abs(rho[i, j] - (xx + 1.0 - dist[j]) / 2.0) < 1e-12
+        order = sorted(range(k), key=lambda j: (dist[j], j))
+        if dist[order[1]] - dist[order[0]] > 1e-9:
+            assert a[i] == order[0]
+            checked += 1
+    assert checked > c.n_docs // 2
+    # update: normalised member sums, densely in plain Python
+    new, norm, sizes = sk.update(c, a, sk.initial_means(c, ids))
+    dense_new = new.dense()
+    for j in range(k):
+        s = [0.0] * c.n_terms
+        for i in range(c.n_docs):
+            if a[i] == j:
+                s = [p + q for p, q in zip(s, X[i])]
+        n2 = math.sqrt(sum(v * v for v in s))
+        assert sizes[j] == int(np.sum(a == j))
+        if n2 > 0:
+            assert abs(norm[j] - n2) < 1e-12
+            assert np.allclose(dense_new[j], [v / n2 for v in s], rtol=0, atol=1e-12)
+
+
+def check_dense_equals_sparse(seed=5):
+    c = tiny_corpus(seed, n_docs=80)
+    m = sk.initial_means(c, dg.init_doc_ids(c.n_docs, 9, seed))
+    dense = sk.similarities(c, m)
+    old = sk.DENSE_LIMIT_BYTES
+    try:
+        sk.DENSE_LIMIT_BYTES = 0
+        sparse = sk.similarities(c, m)
+    finally:
+        sk.DENSE_LIMIT_BYTES = old
+    assert np.array_equal(dense, sparse)
+
+
+def check_k1(seed=3):
+    c = tiny_corpus(seed)
+    its = sk.iterate(c, sk.initial_means(c, [4]), max_iter=3)
+    assert all(np.all(it.assign == 0) for it in its)
+    total = np.zeros(c.n_terms)
+    np.add.at(total, c.term, c.val.astype(np.float64))
+    expect = total / np.linalg.norm(total)
+    assert np.allclose(its[0].means_after.dense()[0], expect, rtol=0, atol=1e-13)
+    assert np.all(np.isinf(its[0].gap))
+
+
+def check_n_equals_k(seed=4):
+    """Every (distinct) object is its own initial mean: by Cauchy-Schwarz it
+    keeps itself, with similarity ||x|| = 1."""
+    c = tiny_corpus(seed, n_docs=30)
+    X = np.array(dense_rows(c))
+    # drop duplicate objects so that Cauchy-Schwarz is strict
+    _, first = np.unique(X.round(12), axis=0, return_index=True)
+    keep = np.sort(first)
+    rows = [(c.term[c.row_ptr[i]:c.row_ptr[i + 1]], c.val[c.row_ptr[i]:c.row_ptr[i + 1]]) for i in keep]
+    c2 = dg.corpus_from_rows(rows, c.n_terms)
+    n = c2.n_docs
+    rho = sk.similarities(c2, sk.initial_means(c2, np.arange(n)))
+    a, best, _ = sk.assign_from_similarities(rho)
+    assert np.array_equal(a, np.arange(n))
+    assert np.allclose(best, 1.0, atol=1e-6)
+
+
+def check_disjoint_supports():
+    """Objects on disjoint term sets have similarity exactly 0 across groups."""
+    rows = [([0, 1], [0.6, 0.8]), ([1, 2], [0.8, 0.6]), ([5, 6], [0.6, 0.8]), ([6, 7], [0.8, 0.6])]
+    c = dg.corpus_from_rows(rows, 8)
+    rho = sk.similarities(c, sk.initial_means(c, [0, 2]))
+    assert rho[0, 1] == 0.0 and rho[1, 1] == 0.0 and rho[2, 0] == 0.0 and rho[3, 0] == 0.0
+    a, _, _ = sk.assign_from_similarities(rho)
+    assert a.tolist() == [0, 0, 1, 1]
+
+
+def check_duplicate_means_tie():
+    c = tiny_corpus(21, n_docs=40)
+    ids = dg.init_doc_ids(c.n_docs, 3, 21)
+    m = sk.initial_means(c, [ids[0], ids[1], ids[0], ids[2]])  # means 0 and 2 identical
+    rho = sk.similarities(c, m)
+    assert np.array_equal(rho[:, 0], rho[:, 2])
+    a, best, gap = sk.assign_from_similarities(rho)
+    assert not np.any(a == 2)  # the lower id of the tied pair always wins
+    tied = a == 0
+    assert np.all(gap[tied] == 0.0)
+
+
+def check_zero_similarity_object():
+    rows = [([0], [1.0]), ([1], [1.0]), ([3], [1.0])]
+    c = dg.corpus_from_rows(rows, 4)
+    rho = sk.similarities(c, sk.initial_means(c, [1, 0]))
+    a, best, gap = sk.assign_from_similarities(rho)
+    assert a.tolist() == [1, 0, 0] and best[2] == 0.0 and gap[2] == 0.0
+
+
+def check_lloyd_invariants(seed=8):
+    """J^r <= sum_j ||s_j^r|| <= J^(r+1); means unit; sum_norm identity."""
+    c = tiny_corpus(seed, n_docs=300, n_terms=60, mean_len=8.0)
+    its = sk.iterate(c, sk.initial_means(c, dg.init_doc_ids(c.n_docs, 12, seed)), max_iter=12)
+    for r, it in enumerate(its):
+        jp = float(np.sum(it.sum_norm))
+        assert it.objective <= jp + 1e-12
+        if r + 1 < len(its):
+            assert jp <= its[r + 1].objective + 1e-12
+        # closed form: sum_{i in C_j} x_i . (s_j/||s_j||) = ||s_j||
+        rho_new = sk.similarities(c, it.means_after)
+        own = rho_new[np.arange(c.n_docs), it.assign]
+        per = np.bincount(it.assign, weights=own, minlength=12)
+        live = it.sizes > 0
+        assert np.allclose(per[live], it.sum_norm[live], rtol=0, atol=1e-12)
+        nrm = np.sqrt(np.bincount(np.repeat(np.arange(12), np.diff(it.means_after.ptr)),
+                                  weights=it.means_after.val ** 2, minlength=12))
+        assert np.allclose(nrm, 1.0, rtol=0, atol=1e-12)
+        assert np.all(np.diff(its[r].assign.shape) == 0)
+
+
+def check_ivf_equals_lloyd(seed=9):
+    """Algorithm 3 keeps the Lloyd solution from the same initial state; with
+    identical means its rho equals Eq. 8's bit for bit (it only skips exact
+    zero products)."""
+    c = tiny_corpus(seed, n_docs=120, n_terms=50)
+    k = 6
+    m0 = sk.initial_means(c, dg.init_doc_ids(c.n_docs, k, seed))
+    xi0 = ivf.inverted_file_from_means(m0)
+    a_ivf, best_ivf, rho_ivf, _ = ivf.assignment_step(c, xi0, k)
+    rho = sk.similarities(c, m0)
+    assert np.array_equal(np.array(rho_ivf), rho)
+    lloyd = sk.iterate(c, m0, max_iter=8)
+    alg3 = ivf.iterate(c, xi0, k, max_iter=8)
+    assert len(lloyd) == len(alg3)
+    for it, (a3, b3, xi3) in zip(lloyd, alg3):
+        assert it.assign.tolist() == a3
+        assert np.allclose(it.best, b3, rtol=0, atol=1e-13)
+        g = it.gap[np.isfinite(it.gap)]
+        assert np.all((g == 0.0) | (g > 1e-9))  # exact ties or clear gaps: no near-ties blur it
+        # same means (Algorithm 3 divides by |C_j| before normalising)
+        mine = it.means_after
+        for j in range(k):
+            mt, mv = mine.row(j)
+            t3 = [p for p in range(c.n_terms) for (cc, _) in xi3[p] if cc == j]
+            u3 = [u for p in range(c.n_terms) for (cc, u) in xi3[p] if cc == j]
+            assert mt.tolist() == t3
+            assert np.allclose(mv, u3, rtol=0, atol=1e-14)
+
+
+def check_multiplication_count(seed=13):
+    """Eq. 15 equals Algorithm 3's counted multiplications and sum_p (no)_p (nc)_p."""
+    c = tiny_corpus(seed, n_docs=100, n_terms=45)
+    m = sk.initial_means(c, dg.init_doc_ids(c.n_docs, 8, seed))
+    xi = ivf.inverted_file_from_means(m)
+    _, _, _, mults = ivf.assignment_step(c, xi, 8)
+    no = np.bincount(c.term, minlength=c.n_terms)
+    nc = np.array([len(xi[p]) for p in range(c.n_terms)])
+    assert sk.multiplication_count(c, m) == mults == int(np.sum(no * nc))
+    # memory identity: sum_p (nc)_p = sum_j (ntm)_j (Section 5.3)
+    assert int(nc.sum()) == int(m.ptr[-1])
+
+
+CHECKS = [check_golden, check_euclidean_brute_force, check_dense_equals_sparse, check_k1,
+          check_n_equals_k, check_disjoint_supports, check_duplicate_means_tie,
+          check_zero_similarity_object, check_lloyd_invariants, check_ivf_equals_lloyd,
+          check_multiplication_count]
+
+
+@pytest.mark.parametrize("check", CHECKS, ids=[f.__name__ for f in CHECKS])
+def test_oracle_pin(check):
+    check()
+
+
+# ------------------------------------------------------- planted mistakes
+
+
+def _mut_drop_last_term(orig):
+    def similarities(corpus, means, rows=None, chunk=2048):
+        keep = np.ones(corpus.nnz, dtype=bool)
+        keep[corpus.row_ptr[1:][np.diff(corpus.row_ptr) > 0] - 1] = False
+        lens = np.diff(corpus.row_ptr) - (np.diff(corpus.row_ptr) > 0)
+        rp = np.zeros_like(corpus.row_ptr)
+        np.cumsum(lens, out=rp[1:])
+        c2 = dg.Corpus(row_ptr=rp, term=corpus.term[keep], val=corpus.val[keep], n_terms=corpus.n_terms)
+        return orig(c2, means, rows, chunk)
+    return "similarities", similarities
+
+
+def _mut_highest_id_ties(orig):
+    def assign_from_similarities(rho):
+        a, best, gap = orig(rho)
+        k = rho.shape[1]
+        a2 = (k - 1 - np.argmax(rho[:, ::-1], axis=1)).astype(np.int32)
+        return a2, best, gap
+    return "assign_from_similarities", assign_from_similarities
+
+
+def _mut_no_normalisation(orig):
+    def update(corpus, assign, prev, empty_policy=0):
+        m, norm, sizes = orig(corpus, assign, prev, empty_policy)
+        owner = np.repeat(np.arange(m.k), np.diff(m.ptr))
+        scale = np.where(norm > 0, norm, 1.0)[owner]
+        return sk.Means(ptr=m.ptr, term=m.term, val=m.val * scale, n_terms=m.n_terms), norm, sizes
+    return "update", update
+
+
+def _mut_shifted_cluster(orig):
+    def cluster_sums(corpus, assign, k):
+        return orig(corpus, (np.asarray(assign) + 1) % k, k)
+    return "cluster_sums", cluster_sums
+
+
+def _mut_reversed_means(orig):
+    def similarities(corpus, means, rows=None, chunk=2048):
+        return orig(corpus, means, rows, chunk)[:, ::-1].copy()
+    return "similarities", similarities
+
+
+def _mut_gap_sign(orig):
+    def assign_from_similarities(rho):
+        a, best, gap = orig(rho)
+        return a, best, -gap
+    return "assign_from_similarities", assign_from_similarities
+
+
+MUTANTS = [_mut_drop_last_term, _mut_highest_id_ties, _mut_no_normalisation, _mut_shifted_cluster,
+           _mut_reversed_means, _mut_gap_sign]
+
+
+@pytest.mark.parametrize("mutant", MUTANTS, ids=[m.__name__ for m in MUTANTS])
+def test_planted_mistakes_are_caught(mutant, monkeypatch):
+    name, fn = mutant(getattr(sk, name_of(mutant)))
+    monkeypatch.setattr(sk, name, fn)
+    failed = []
+    for check in CHECKS:
+        try:
+            check()
+        except (AssertionError, ValueError, IndexError):
+            failed.append(check.__name__)
+    assert failed, f"no pin caught {mutant.__name__}"
+
+
+def name_of(mutant):
+    return {
+        _mut_drop_last_term: "similarities", _mut_highest_id_ties: "assign_from_similarities",
+        _mut_no_normalisation: "update", _mut_shifted_cluster: "cluster_sums",
+        _mut_reversed_means: "similarities", _mut_gap_sign: "assign_from_similarities",
+    }[mutant]
