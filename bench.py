@@ -1,0 +1,357 @@
+"""Benchmark: seconds per Lloyd iteration of inverted-file spherical k-means.
+
+Default workload: 1,000,000 synthetic Zipf documents over 500,000 terms
+(lognormal lengths, mean 120), K = 10,000, FP32 storage.  One step = one full
+Lloyd iteration (assignment step + update step) through the C ABI; inputs are
+resident in HBM when the timed region starts and are larger than L2 (CSR
+0.96 GB).  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload NAME] [--storage f32|f16|bf16]
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of each iteration, scaled to the whole workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sec/Lloyd iteration & assign-step HBM GB/s (% peak); mixed vs FP32 at equal assigns"
+UNIT = "s/iter"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "assign_kernel_dram_traffic.txt")
+ASSIGN_SRC = os.path.join(ROOT, "paper_2002_09094_gb300", "csrc", "assign.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="ivf-scale-n1m-d500k-k10k")
+    p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_per_launch(n_docs: int, storage: str):
+    """DRAM bytes per assignment launch from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    try:
+        text = open(TRAFFIC_FILE).read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(open(ASSIGN_SRC, "rb").read()).hexdigest()
+    m_sha = re.search(r"assign_cu_sha256:\s*([0-9a-f]+)", text)
+    if not m_sha or m_sha.group(1) != sha:
+        return None
+    m = re.search(rf"bytes_per_launch\[{storage}\]:\s*([0-9.eE+]+)", text)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_iteration_sample(corpus, means, assign_for_update, rng, budget_s: float):
+    """Time the FP64 oracle on a bounded sample and scale to the whole workload.
+
+    Assignment: similarities + argmax for S sampled objects, scaled by N/S.
+    Update: member sums + normalisation over the objects of a contiguous row
+    range, scaled by nnz / nnz(range).  Returns (seconds per iteration, sample text).
+    """
+    import oracle.spherical_kmeans as sk
+    from paper_2002_09094_gb300 import datagen as dg
+
+    n = corpus.n_docs
+    # size the sample from a short probe
+    probe = rng.choice(n, size=min(n, 64), replace=False)
+    t = time.perf_counter()
+    sk.assign_from_similarities(sk.similarities(corpus, means, probe))
+    per_obj = max((time.perf_counter() - t) / len(probe), 1e-7)
+    s = int(min(n, max(64, 0.6 * budget_s / per_obj)))
+    rows = rng.choice(n, size=s, replace=False)
+    t = time.perf_counter()
+    sk.assign_from_similarities(sk.similarities(corpus, means, rows))
+    t_assign = (time.perf_counter() - t) * n / s
+    # update over a leading row range: probe 1% of the rows, then grow the
+    # range to about 40% of the budget
+    def timed_update(hi):
+        sub = dg.Corpus(row_ptr=corpus.row_ptr[:hi + 1].copy(), term=corpus.term[:corpus.row_ptr[hi]],
+                        val=corpus.val[:corpus.row_ptr[hi]], n_terms=corpus.n_terms)
+        t = time.perf_counter()
+        sk.update(sub, assign_for_update[:hi], means)
+        return time.perf_counter() - t, sub
+
+    hi = max(1, n // 100)
+    dt, sub = timed_update(hi)
+    grow = 0.4 * budget_s / max(dt, 1e-4)
+    if grow > 2.0 and hi < n:
+        hi = int(min(n, hi * grow))
+        dt, sub = timed_update(hi)
+    t_update = dt * corpus.nnz / max(1, sub.nnz)
+    desc = (f"oracle assignment of {s} random objects scaled x{n / s:.1f}; oracle update over the first "
+            f"{hi} objects ({sub.nnz} tuples) scaled x{corpus.nnz / max(1, sub.nnz):.1f}")
+    return t_assign + t_update, desc
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on a bounded sample per step."""
+    if rank != 0:
+        return
+    import oracle.spherical_kmeans as sk
+    from paper_2002_09094_gb300 import datagen as dg
+
+    w = dg.WORKLOADS[args.workload]
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    means = sk.initial_means(c, ids)
+    rng = np.random.default_rng(0)
+    budget = max(2.0, min(args.cpu_seconds, 240.0 / max(1, args.steps + args.warmup)))
+    assign_guess = rng.integers(0, w.k, size=c.n_docs).astype(np.int32)
+    vals, desc = [], ""
+    for step in range(args.warmup + args.steps):
+        v, desc = oracle_iteration_sample(c, means, assign_guess, rng, budget)
+        if step >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    cores = 1
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": w.name, "n_docs": c.n_docs, "n_terms": c.n_terms, "nnz": c.nnz, "k": w.k,
+                     "means": "seeded initial means (K documents), first iteration"},
+          "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+          "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2002_09094_gb300 import build as cuda_build
+    from paper_2002_09094_gb300 import datagen as dg
+    from paper_2002_09094_gb300 import ivf
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = dg.WORKLOADS[args.workload]
+    t0 = time.time()
+    c = dg.make_corpus(w.corpus)
+    gen_s = time.time() - t0
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    stream = torch.cuda.Stream()
+    bv = 4 if args.storage == "f32" else 2
+    with torch.cuda.stream(stream):
+        m = ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage, stream=stream.cuda_stream)
+        m.set_means_from_docs(ids)
+        for _ in range(args.warmup):
+            m.assign(stats=False)
+            m.update()
+        torch.cuda.synchronize()
+        barrier()
+        # ---------------------------------------------------------- timed region
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        m.timing_reset(True)
+        launches0 = ivf.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            m.assign(stats=False)
+            m.update()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total_ms = ev0.elapsed_time(ev1)
+        launches = ivf.launch_count() - launches0
+        clk = clocks.stop()
+        timing = m.get_timing()
+        m.timing_reset(False)
+        info = m.info()
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        # ------------------------------------------------------ end to end
+        # each step: host->device copy of the objects from pinned memory, one
+        # iteration, device->host read of the assignment
+        rp_h = torch.from_numpy(c.row_ptr).pin_memory()
+        tm_h = torch.from_numpy(c.term).pin_memory()
+        vl_h = torch.from_numpy(c.val).pin_memory()
+        out_h = torch.empty(c.n_docs, dtype=torch.int32).pin_memory()
+        h2d = rp_h.numel() * 8 + tm_h.numel() * 4 + vl_h.numel() * 4
+        d2h = out_h.numel() * 4
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            m.load_objects(rp_h, tm_h, vl_h)
+            m.assign(stats=False)
+            m.update()
+            m.get_assign(out_h)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / max(1, args.e2e_steps)
+        # current state for the CPU baseline sample
+        means_np = m.get_means()
+        assign_np = m.get_assign()
+        m.close()
+
+    ms_per_step = total_ms / args.steps
+    n_steps = max(1, timing["n_assign"])
+    kern_ms = timing["assign_kernel_ms"] / n_steps
+    entries = timing["entries_visited"] / n_steps
+    b_assign = c.nnz * (4 + bv) + 8 * (c.n_docs + 1) + entries * (2 + bv) + c.n_docs * 12
+    peak, peak_kind = peaks()
+    achieved = b_assign / (kern_ms / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(c.n_docs, args.storage),
+            "kernel": "k_assign", "peak_source": f"{peak_kind} hbm_gbs",
+            "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
+            "kernel_ms": round(kern_ms, 4)}
+    out = {"metric": METRIC, "value": ms_per_step / 1e3 / world, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic", "impl": "ours",
+           "config": {"workload": w.name, "n_docs": c.n_docs, "n_terms": c.n_terms, "nnz": c.nnz, "k": w.k,
+                      "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2 (CSR %.2f GB); no flush" % (c.nnz * 8 / 1e9),
+                      "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"],
+                      "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},
+           "phases_ms_per_step": {"assign_kernel": round(kern_ms, 4),
+                                  "assign_step": round(timing["assign_step_ms"] / n_steps, 4),
+                                  "update": round(timing["update_ms"] / max(1, timing["n_update"]), 4)},
+           "roofline": roof,
+           "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)},
+           "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle.spherical_kmeans as sk
+
+        ptr, term, val = means_np
+        means = sk.Means(ptr=ptr, term=term.astype(np.int64), val=val, n_terms=c.n_terms)
+        v, desc = oracle_iteration_sample(c, means, assign_np, np.random.default_rng(1), args.cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": desc + "; means = the GPU's current FP64 means"}
+    if rank == 0:
+        emit(out)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * ivf.h -- C ABI of libivfkm: inverted-file spherical k-means (IVF) on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * The method is the Lloyd iteration of Aoyama, Saito and Ikeda,
+ * "Inverted-File k-Means Clustering: Performance Analysis" (arXiv 2002.09094):
+ *   - problem: spherical k-means, Section 2.2, Eqs. 4-5, Algorithm 2 -- N
+ *     unit-L2 sparse objects, K unit-L2 means, maximise the summed cosine
+ *     similarity;
+ *   - data structures: objects in the standard sparse expression (Section
+ *     2.3, Fig. 1(a)) = CSR rows of (term id, value) sorted by term id; means
+ *     in the inverted-file expression (Section 3) = for every term s the list
+ *     xi_s of (cluster id c, value u) in ascending c;
+ *   - one iteration (Algorithm 3): the assignment step scatters
+ *     rho_c += v * u over the posting lists of the object's terms and takes
+ *     the argmax; the update step sums each cluster's members, normalises,
+ *     and rebuilds the inverted file.
+ *
+ * Conventions (all calls):
+ *   - Ids are 0-based (the paper counts from 1).
+ *   - Input arrays may be host or device pointers (the library copies them
+ *     with cudaMemcpyDefault); the library never keeps a caller pointer.
+ *     Output arrays of ivf_assign are DEVICE pointers (or NULL); the
+ *     ivf_get_* calls write to host or device pointers.
+ *   - Every call is ordered on the CUDA stream given at create time and
+ *     returns after enqueueing, except where a comment says it synchronises.
+ *   - Errors come back as an ivf_status; the library never aborts or traps.
+ *     After IVF_E_INVALID or IVF_E_STATE the context is unchanged and still
+ *     usable; after IVF_E_CUDA destroy it.  ivf_last_error() gives a message.
+ *   - Ties in the argmax go to the lowest cluster id (an object that shares
+ *     no term with any mean therefore goes to cluster 0).  An empty cluster
+ *     keeps its previous mean (empty_policy 0) or gets an empty mean
+ *     (empty_policy 1).  A mean element that sums to exactly 0 is dropped,
+ *     as Algorithm 3's "w_p != 0" test does.
+ */
+#ifndef IVFKM_IVF_H
+#define IVFKM_IVF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ivf_ctx ivf_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  IVF_OK = 0,
+  IVF_E_INVALID = 1,     /* bad argument or malformed input; nothing changed */
+  IVF_E_STATE = 2,       /* call out of order (e.g. assign before set_means) */
+  IVF_E_OOM = 3,         /* device allocation failed or a capacity was exceeded */
+  IVF_E_CUDA = 4,        /* a CUDA call failed; destroy the context */
+  IVF_E_TIMEOUT = 5,     /* a bounded device wait ran out */
+  IVF_E_UNSUPPORTED = 6  /* valid request this build does not handle */
+} ivf_status;
+
+/* Storage type of the object and mean values streamed by the assignment
+ * step.  Accumulation is FP32 in every case; FP32 master copies of the
+ * object values and FP64 master means are kept for the update step and the
+ * FP64 re-score. */
+typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
+
+/* ivf_config.flags */
+#define IVF_FLAG_VALIDATE 1u  /* check CSR rows (sorted, unique, in range, finite) at create/load */
+#define IVF_FLAG_NO_GRAPH 2u  /* ivf_iterate launches kernels directly instead of a CUDA graph */
+
+typedef struct {
+  int64_t n_docs;      /* N >= 1 */
+  int64_t n_terms;     /* D >= 1 */
+  int64_t nnz;         /* number of (term, value) tuples over all objects */
+  int32_t k;           /* number of clusters, 1 <= k <= N */
+  int32_t storage;     /* ivf_dtype */
+  int32_t rescore;     /* 1: FP64 re-score of objects whose top-2 gap is within the
+                          computed error bound (default and required for exact
+                          assignments); 0: off */
+  int32_t empty_policy;/* 0 keep previous mean (default), 1 empty mean */
+  int32_t k_tile;      /* accumulator tile over the cluster range: 0 = autotune,
+                          else a power of two in [512, 65536] or >= k (no tiling) */
+  int32_t warps_per_block; /* 0 = autotune, else 1..32 */
+  uint32_t flags;      /* IVF_FLAG_* */
+  int32_t reserved;
+} ivf_config;
+
+/* Per-iteration statistics (Section 5.2 reports time and memory per
+ * iteration; Eq. 15 counts the multiplications). */
+typedef struct {
+  int64_t n_changed;       /* objects whose assignment differs from the previous one
+                              (all N on the first assignment) */
+  int64_t entries_visited; /* posting entries multiplied: sum_i sum_h (nc)_{t_(i,h)}, Eq. 15 */
+  int64_t ivf_entries;     /* E = sum_p (nc)_p, tuples in the inverted file used */
+  int64_t n_zero_sim;      /* objects whose best similarity is exactly 0 */
+  int64_t n_flagged;       /* objects whose FP32 top-2 gap was within the error bound */
+  int64_t n_rescored;      /* objects re-scored in FP64 */
+  double objective;        /* J = sum_i rho(x_i, mu_a(i)), Eq. 5, FP64 accumulation */
+  float t_assign_ms;       /* device time of the last assignment step (0 if not timed) */
+  float t_update_ms;       /* device time of the last update step (0 if not timed) */
+} ivf_iter_stats;
+
+typedef struct {
+  int64_t n_docs, n_terms, nnz;
+  int32_t k, n_instances;
+  int64_t ivf_entries;     /* E of the current means */
+  int64_t ivf_capacity;    /* maximum E the context can hold */
+  int32_t k_tile, warps_per_block; /* launch shape in use (after autotune) */
+  int32_t iteration;       /* completed update steps */
+  int32_t storage;
+  int64_t device_bytes;    /* device memory held by the context */
+} ivf_info;
+
+/* Create a context for one clustering problem and copy the objects in.
+ * row_ptr: int64[N+1], row_ptr[0] = 0, row_ptr[N] = nnz, non-decreasing.
+ * term: int32[nnz], ascending and unique inside each row, in [0, D).
+ * val: float[nnz], finite; each row is expected to have unit L2 norm
+ *      (Section 2.2: objects are points on the unit hypersphere).
+ * cuda_stream: cudaStream_t for all work of the context (NULL = legacy default).
+ * On success *out holds the context; on error *out is NULL. */
+ivf_status ivf_create(const ivf_config* cfg, const int64_t* row_ptr, const int32_t* term,
+                      const float* val, void* cuda_stream, ivf_ctx** out);
+
+/* Replace the object values and terms (same N and nnz as at create time):
+ * the host->device copy of a new batch of objects.  Row structure may
+ * change.  Means and assignments are kept. */
+ivf_status ivf_load_objects(ivf_ctx* ctx, const int64_t* row_ptr, const int32_t* term,
+                            const float* val);
+
+/* Set the K means from cluster-major sparse rows (mean j = row j):
+ * mean_ptr int64[K+1], mean_term int32[E0] ascending and unique per row,
+ * mean_val float[E0].  Each row is divided by its FP64 L2 norm (Algorithm
+ * 2's normalisation); a row of zero norm is IVF_E_INVALID.  The inverted
+ * file (Section 3) is built from the result.  Resets the iteration count and
+ * forgets previous assignments. */
+ivf_status ivf_set_means(ivf_ctx* ctx, const int64_t* mean_ptr, const int32_t* mean_term,
+                         const float* mean_val);
+
+/* Initial means from K distinct objects: mean j = x_{doc_ids[j]} / ||x||
+ * (Section 5.3: the initial state is chosen at random).  doc_ids: int32[K]. */
+ivf_status ivf_set_means_from_docs(ivf_ctx* ctx, const int32_t* doc_ids);
+
+/* Assignment step of Algorithm 3 (the triple loop and the argmax) for all
+ * objects against the current means, then the FP64 re-score of near-ties
+ * and the reductions for the statistics.
+ * assign_out: device int32[N] or NULL; best_out: device float[N] or NULL
+ * (rho of the chosen cluster); gap_out: device float[N] or NULL (best minus
+ * second best).  The results also stay in the context for ivf_update.
+ * stats_out: host pointer or NULL; when given, the call synchronises the
+ * stream and fills it. */
+ivf_status ivf_assign(ivf_ctx* ctx, int32_t* assign_out, float* best_out, float* gap_out,
+                      ivf_iter_stats* stats_out);
+
+/* Update step of Algorithm 3 from the last assignment: member sums in FP64,
+ * L2 normalisation, inverted-file rebuild. */
+ivf_status ivf_update(ivf_ctx* ctx);
+
+/* Run assignment + update until no assignment changes (from the second
+ * iteration on) or max_iter iterations.  Synchronises once per iteration to
+ * read the change count.  iters_done / converged / last_stats may be NULL. */
+ivf_status ivf_iterate(ivf_ctx* ctx, int32_t max_iter, int32_t* iters_done, int32_t* converged,
+                       ivf_iter_stats* last_stats);
+
+/* Copies out (host or device destination; these synchronise the stream). */
+ivf_status ivf_get_assign(ivf_ctx* ctx, int32_t* out);        /* int32[N] */
+ivf_status ivf_get_best(ivf_ctx* ctx, float* out);            /* float[N] */
+ivf_status ivf_get_gap(ivf_ctx* ctx, float* out);             /* float[N] */
+ivf_status ivf_get_info(ivf_ctx* ctx, ivf_info* out);         /* host */
+/* FP64 master means, cluster-major: ptr int64[K+1], term int32[E], val double[E];
+ * any of the three may be NULL. */
+ivf_status ivf_get_means(ivf_ctx* ctx, int64_t* ptr, int32_t* term, double* val);
+/* The inverted file as streamed by the assignment: term_ptr int64[D+1],
+ * cid int32[E] (cluster ids), w float[E] (values after the storage cast,
+ * widened to float); any may be NULL. */
+ivf_status ivf_get_inverted_file(ivf_ctx* ctx, int64_t* term_ptr, int32_t* cid, float* w);
+/* Clusters C_j of the last update: cl_ptr int64[K+1], members int32[N] in
+ * ascending object id inside each cluster; either may be NULL. */
+ivf_status ivf_get_members(ivf_ctx* ctx, int64_t* cl_ptr, int32_t* members);
+/* Set the "previous" assignment used for n_changed (checkpoint resume). */
+ivf_status ivf_set_assign(ivf_ctx* ctx, const int32_t* assign);
+/* Restore FP64 master means exactly (checkpoint resume), cluster-major as
+ * returned by ivf_get_means; no renormalisation. */
+ivf_status ivf_restore_means(ivf_ctx* ctx, const int64_t* ptr, const int32_t* term,
+                             const double* val, int32_t iteration);
+
+/* Message of the last error on this context (never NULL). */
+const char* ivf_last_error(const ivf_ctx* ctx);
+/* Frees everything the context holds.  NULL is a no-op. */
+void ivf_destroy(ivf_ctx* ctx);
+
+/* Device-time accounting over a window of calls (Section 5.2 measures CPU
+ * time per iteration; this is its GPU counterpart).  While enabled, every
+ * ivf_assign / ivf_update call records CUDA events on the context stream
+ * around its kernels; nothing synchronises until ivf_get_timing. */
+typedef struct {
+  int32_t n_assign;         /* ivf_assign calls in the window */
+  int32_t n_update;         /* ivf_update calls in the window */
+  double assign_kernel_ms;  /* sum: the assignment kernel alone */
+  double assign_step_ms;    /* sum: assignment kernel + FP64 re-score + reductions */
+  double update_ms;         /* sum: update step including the inverted-file rebuild */
+  int64_t entries_visited;  /* sum of the Eq. 15 multiplication counts */
+  int64_t n_rescored;       /* sum of objects re-scored in FP64 */
+} ivf_timing;
+/* Start a new window (enable = 1) or stop recording (enable = 0). */
+ivf_status ivf_timing_reset(ivf_ctx* ctx, int32_t enable);
+/* Sums over the window so far; synchronises the stream. */
+ivf_status ivf_get_timing(ivf_ctx* ctx, ivf_timing* out);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t ivf_launch_count(void);
+/* Library version string. */
+const char* ivf_version(void);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent clustering problems of uneven N, K and D
+ * in one context.  Every launch (assignment, re-score, update) covers all
+ * instances at once; each instance's result is identical to running it
+ * alone, because no arithmetic mixes instances.
+ * inst_docs int64[n_inst+1]: object offsets (row_ptr is the concatenation of
+ *   the instances' CSR rows, term ids local to the instance);
+ * inst_terms int32[n_inst]: D of each instance; inst_k int32[n_inst]: K.
+ * cfg supplies storage, rescore, empty_policy, k_tile, warps, flags;
+ * cfg->n_docs/n_terms/nnz/k are ignored (taken from the arrays).
+ * Means: ivf_set_means_from_docs with doc_ids int32[sum K] holding each
+ * instance's K local document ids in instance order.  ivf_get_assign
+ * returns local cluster ids. ------------------------------------------- */
+ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* inst_docs,
+                       const int32_t* inst_terms, const int32_t* inst_k, const int64_t* row_ptr,
+                       const int32_t* term, const float* val, void* cuda_stream, ivf_ctx** out);
+/* Per-instance change counts of the last assignment: int64[n_inst] (host or device). */
+ivf_status ivfb_get_changed(ivf_ctx* ctx, int64_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IVFKM_IVF_H */

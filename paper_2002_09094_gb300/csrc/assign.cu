@@ -1,0 +1,481 @@
+// Assignment step of Algorithm 3 (IVF) on sm_103a, the FP64 re-score of
+// near-ties, and the per-iteration reductions.
+//
+// Kernel design (GB300-first, not the paper's CPU loop nest):
+//   * persistent grid, one warp per object, objects handed out by an atomic
+//     counter (object cost sum_h (nc)_{t_(i,h)} is heavy tailed);
+//   * each warp owns a private FP32 accumulator rho over a tile of the
+//     cluster range in shared memory (Algorithm 3's rho in R^k, tiled when k
+//     is large: per-(term, tile) offsets give each posting list's slice);
+//   * the object's terms are taken one at a time and the 32 lanes stride over
+//     that term's posting list xi_s: cluster ids are unique inside a list, so
+//     rho_c += v * u needs no atomics, and every rho_c is summed in ascending
+//     term order -- bit-reproducible from run to run and across tile shapes;
+//   * argmax by a per-lane scan plus a warp butterfly on (value desc, id asc),
+//     which also yields the runner-up for the top-2 gap;
+//   * objects whose gap lies within the computed FP32 / FP16 / BF16 error
+//     bound are queued with their candidate clusters for an FP64 re-score
+//     against the FP64 master means, so the returned assignment is the FP64
+//     argmax.
+#include <float.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace ivfk {
+
+namespace {
+
+constexpr int kMaxThreads = 1024;
+
+__device__ __forceinline__ void top2_push(float& b, int& id, float& s, float x, int xid) {
+  if (x > b || (x == b && xid < id)) {
+    s = b;
+    b = x;
+    id = xid;
+  } else if (x > s) {
+    s = x;
+  }
+}
+
+__device__ __forceinline__ void top2_merge(float& b, int& id, float& s, float b2, int id2, float s2) {
+  if (b2 > b || (b2 == b && id2 < id)) {
+    s = fmaxf(s2, b);
+    b = b2;
+    id = id2;
+  } else {
+    s = fmaxf(s, b2);
+  }
+}
+
+__device__ __forceinline__ void warp_top2(float& b, int& id, float& s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float b2 = __shfl_xor_sync(IVF_FULL_MASK, b, o);
+    const int id2 = __shfl_xor_sync(IVF_FULL_MASK, id, o);
+    const float s2 = __shfl_xor_sync(IVF_FULL_MASK, s, o);
+    top2_merge(b, id, s, b2, id2, s2);
+  }
+}
+
+__device__ __forceinline__ int find_instance(const int64_t* offs, int n_inst, int64_t x) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Upper bound on |rho_hat - rho| for one object against any unit mean, where
+// rho is exact with the FP64 master mean and rho_hat the FP32 accumulation of
+// the stored (rounded) values.  m = number of object terms (>= number of
+// products summed into any rho_c), nx >= ||x||_2.
+//   FP32: mean rounding u*S plus FMA recursive summation gamma_m * S(1+u).
+//   FP16/BF16: both operands rounded (u' = u16 + 2u for the FP64->FP32->16
+//   double rounding), products exact in FP32, plus the FP16 subnormal floor
+//   and gamma_m on the summed magnitudes.
+__device__ __forceinline__ float err_bound(int m, float nx, int storage) {
+  const float u32 = 5.9604645e-08f;  // 2^-24
+  const float S = nx * 1.000001f;
+  const float fm = (float)m;
+  const float g = fm * u32 / (1.f - fm * u32);
+  float e;
+  if (storage == ST_F32) {
+    e = S * (u32 + g * (1.f + u32));
+  } else {
+    const float u16 = storage == ST_F16 ? 4.8828125e-04f : 3.90625e-03f;
+    const float up = u16 + 2.f * u32;
+    const float sub = storage == ST_F16 ? fm * u32 * (1.f + up) : fm * 1e-37f;
+    const float mag = S * (1.f + up) * (1.f + up) + sub;
+    e = S * (2.f * up + up * up) + sub + g * mag;
+  }
+  return e * 1.0001f;
+}
+
+// Drop candidates below thr (warp-cooperative, ncand uniform across lanes).
+__device__ __forceinline__ void prune_candidates(int* cand_id, float* cand_val, int& ncand, float thr, int lane) {
+  if (ncand == 0) return;
+  int idv = 0;
+  float vv = -INFINITY;
+  bool keep = false;
+  if (lane < ncand) {
+    idv = cand_id[lane];
+    vv = cand_val[lane];
+    keep = vv >= thr;
+  }
+  const unsigned km = __ballot_sync(IVF_FULL_MASK, keep);
+  __syncwarp();
+  if (keep) {
+    const int pos = __popc(km & ((1u << lane) - 1u));
+    cand_id[pos] = idv;
+    cand_val[pos] = vv;
+  }
+  ncand = __popc(km);
+  __syncwarp();
+}
+
+template <typename WT>
+__global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
+  extern __shared__ __align__(16) float smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* rho = smem + (size_t)warp * (a.tile_cap + 2 * CAND_MAX);
+  int* cand_id = reinterpret_cast<int*>(rho + a.tile_cap);
+  float* cand_val = rho + a.tile_cap + CAND_MAX;
+  const WT* __restrict__ val = static_cast<const WT*>(a.val);
+  const WT* __restrict__ w = static_cast<const WT*>(a.w);
+  const uint16_t* __restrict__ cid = a.cid;
+  const int cmask = a.tiled ? (a.k_tile - 1) : 0xFFFF;
+  const unsigned lt = (1u << lane) - 1u;
+  unsigned long long my_entries = 0;
+
+  for (;;) {
+    unsigned long long o = 0;
+    if (lane == 0) o = atomicAdd(a.work, 1ull);
+    o = __shfl_sync(IVF_FULL_MASK, o, 0);
+    if (o >= (unsigned long long)a.n_docs) break;
+    const int64_t i = (int64_t)o;
+    const int b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
+    const int K = a.inst_clu[b + 1] - a.inst_clu[b];
+    const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
+    const int m = (int)(r1 - r0);
+    const float e2 = a.rescore ? 2.f * err_bound(m, a.nx[i], a.storage) : -1.f;
+    const int tile = a.tiled ? a.k_tile : K;
+    const int n_tiles = a.tiled ? (K + a.k_tile - 1) / a.k_tile : 1;
+    float best = -INFINITY, second = -INFINITY;
+    int bid = 0x7fffffff;
+    int ncand = 0;
+    bool overflow = false;
+
+    for (int tt = 0; tt < n_tiles; ++tt) {
+      const int lo = tt * tile;
+      const int cnt = min(tile, K - lo);
+      // rho <- 0 over the tile
+      float4* r4 = reinterpret_cast<float4*>(rho);
+      for (int q = lane; q < ((cnt + 3) >> 2); q += 32) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+      // for s in S_i (32 at a time): for (c, u) in xi_s: rho_c += v * u
+      for (int64_t h0 = r0; h0 < r1; h0 += 32) {
+        const int64_t h = h0 + lane;
+        int64_t beg = 0;
+        int len = 0;
+        float v = 0.f;
+        if (h < r1) {
+          const int t = __ldg(a.term + h);
+          v = to_f32(val[h]);
+          const int64_t tb = __ldg(a.term_ptr + t);
+          if (a.tiled) {
+            const int32_t* to = a.toff + (int64_t)t * (a.n_tiles_max + 1) + tt;
+            const int o0 = __ldg(to), o1 = __ldg(to + 1);
+            beg = tb + o0;
+            len = o1 - o0;
+          } else {
+            beg = tb;
+            len = (int)(__ldg(a.term_ptr + t + 1) - tb);
+          }
+        }
+        my_entries += (unsigned long long)len;
+        const int nh = (int)min((int64_t)32, r1 - h0);
+        for (int j = 0; j < nh; ++j) {
+          const int64_t bj = __shfl_sync(IVF_FULL_MASK, beg, j);
+          const int lj = __shfl_sync(IVF_FULL_MASK, len, j);
+          const float vj = __shfl_sync(IVF_FULL_MASK, v, j);
+          const uint16_t* __restrict__ cp = cid + bj;
+          const WT* __restrict__ wp = w + bj;
+          int q = lane;
+          for (; q + 96 < lj; q += 128) {
+            const int c0 = __ldg(cp + q) & cmask;
+            const int c1 = __ldg(cp + q + 32) & cmask;
+            const int c2 = __ldg(cp + q + 64) & cmask;
+            const int c3 = __ldg(cp + q + 96) & cmask;
+            const float u0 = to_f32(wp[q]);
+            const float u1 = to_f32(wp[q + 32]);
+            const float u2 = to_f32(wp[q + 64]);
+            const float u3 = to_f32(wp[q + 96]);
+            rho[c0] = fmaf(vj, u0, rho[c0]);
+            rho[c1] = fmaf(vj, u1, rho[c1]);
+            rho[c2] = fmaf(vj, u2, rho[c2]);
+            rho[c3] = fmaf(vj, u3, rho[c3]);
+          }
+          for (; q < lj; q += 32) {
+            const int c = __ldg(cp + q) & cmask;
+            rho[c] = fmaf(vj, to_f32(wp[q]), rho[c]);
+          }
+          __syncwarp();
+        }
+      }
+      // argmax over the tile: lowest id among the maxima, plus the runner-up
+      float tb = -INFINITY, ts = -INFINITY;
+      int ti = 0x7fffffff;
+      for (int q = lane; q < cnt; q += 32) top2_push(tb, ti, ts, rho[q], lo + q);
+      warp_top2(tb, ti, ts);
+      top2_merge(best, bid, second, tb, ti, ts);
+      if (e2 >= 0.f) {
+        const float thr = best - e2;
+        prune_candidates(cand_id, cand_val, ncand, thr, lane);
+        if (ts >= thr) {
+          for (int q0 = 0; q0 < cnt; q0 += 32) {
+            const int q = q0 + lane;
+            const float x = q < cnt ? rho[q] : -INFINITY;
+            const bool p = x >= thr;
+            const unsigned pm = __ballot_sync(IVF_FULL_MASK, p);
+            if (p) {
+              const int pos = ncand + __popc(pm & lt);
+              if (pos < CAND_MAX) {
+                cand_id[pos] = lo + q;
+                cand_val[pos] = x;
+              }
+            }
+            ncand += __popc(pm);
+            if (ncand > CAND_MAX) {
+              overflow = true;
+              ncand = CAND_MAX;
+            }
+          }
+        } else if (tb >= thr) {
+          if (ncand < CAND_MAX) {
+            if (lane == 0) {
+              cand_id[ncand] = ti;
+              cand_val[ncand] = tb;
+            }
+            ++ncand;
+          } else {
+            overflow = true;
+          }
+        }
+      }
+      __syncwarp();
+    }
+
+    const float g = best - second;
+    if (lane == 0) {
+      a.assign[i] = bid;
+      a.best[i] = best;
+      a.gap[i] = g;
+    }
+    if (e2 >= 0.f && g <= e2) {
+      prune_candidates(cand_id, cand_val, ncand, best - e2, lane);
+      unsigned slot = 0;
+      if (lane == 0) slot = atomicAdd(a.n_flagged, 1u);
+      slot = __shfl_sync(IVF_FULL_MASK, slot, 0);
+      if (lane == 0) {
+        a.flag_obj[slot] = (int32_t)i;
+        a.flag_cnt[slot] = overflow ? -1 : ncand;
+      }
+      if (!overflow && lane < ncand) a.flag_cand[(int64_t)slot * CAND_MAX + lane] = cand_id[lane];
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_entries += __shfl_xor_sync(IVF_FULL_MASK, my_entries, o);
+  if (lane == 0 && my_entries) atomicAdd(a.entries, my_entries);
+}
+
+// ------------------------------------------------------------- re-score
+
+__device__ __forceinline__ void top2_push_d(double& b, int& id, double& s, double x, int xid) {
+  if (x > b || (x == b && xid < id)) {
+    s = b;
+    b = x;
+    id = xid;
+  } else if (x > s) {
+    s = x;
+  }
+}
+
+// One warp per flagged object: rho_ij in FP64 for its candidate clusters (all
+// clusters on overflow) against the FP64 master means, summed in ascending h
+// as Eq. 8 writes it, then the argmax with the lowest-id tie rule.
+__global__ void __launch_bounds__(256) k_rescore(const RescoreArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nf = (int64_t)*a.n_flagged;
+  for (int64_t slot = gw; slot < nf; slot += nw) {
+    const int64_t i = a.flag_obj[slot];
+    const int cnt = a.flag_cnt[slot];
+    const int b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
+    const int c0 = a.inst_clu[b];
+    const int K = a.inst_clu[b + 1] - c0;
+    const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
+    const int ncl = cnt < 0 ? K : cnt;
+    double best = -INFINITY, second = -INFINITY;
+    int bid = 0x7fffffff;
+    for (int q = 0; q < ncl; ++q) {
+      const int c = cnt < 0 ? q : a.flag_cand[slot * CAND_MAX + q];
+      const int64_t mb = a.mptr[c0 + c], me = a.mptr[c0 + c + 1];
+      double acc = 0.0;
+      for (int64_t h0 = r0; h0 < r1; h0 += 32) {
+        const int64_t h = h0 + lane;
+        double p = 0.0;
+        bool hit = false;
+        if (h < r1) {
+          const int t = a.term[h];
+          int64_t lo = mb, hi = me;
+          while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.mterm[mid] < t)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          if (lo < me && a.mterm[lo] == t) {
+            p = __dmul_rn((double)a.val32[h], a.mval[lo]);
+            hit = true;
+          }
+        }
+        const unsigned hm = __ballot_sync(IVF_FULL_MASK, hit);
+        const int nh = (int)min((int64_t)32, r1 - h0);
+        for (int j = 0; j < nh; ++j) {
+          const double pj = __shfl_sync(IVF_FULL_MASK, p, j);
+          if ((hm >> j) & 1u) acc = __dadd_rn(acc, pj);
+        }
+      }
+      top2_push_d(best, bid, second, acc, c);
+    }
+    if (lane == 0) {
+      a.assign[i] = bid;
+      a.best[i] = __double2float_rn(best);
+      a.gap[i] = __double2float_rn(best - second);
+      atomicAdd(a.n_rescored, 1ull);
+    }
+  }
+}
+
+// ------------------------------------------------------------ reductions
+
+constexpr int RED_THREADS = 256;
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs a) {
+  double obj = 0.0;
+  unsigned long long ch = 0, zs = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_docs; i += stride) {
+    const float bst = a.best[i];
+    obj += (double)bst;
+    zs += (bst == 0.f) ? 1ull : 0ull;
+    const bool changed = a.prev == nullptr || a.assign[i] != a.prev[i];
+    if (changed) {
+      ++ch;
+      if (a.n_inst > 1)
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.inst_changed) + find_instance(a.inst_docs, a.n_inst, i),
+                  1ull);
+    }
+  }
+  __shared__ double so[RED_THREADS / 32];
+  __shared__ unsigned long long sc[RED_THREADS / 32], sz[RED_THREADS / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    obj += __shfl_down_sync(IVF_FULL_MASK, obj, o);
+    ch += __shfl_down_sync(IVF_FULL_MASK, ch, o);
+    zs += __shfl_down_sync(IVF_FULL_MASK, zs, o);
+  }
+  if (lane == 0) {
+    so[warp] = obj;
+    sc[warp] = ch;
+    sz[warp] = zs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    unsigned long long c = 0, z = 0;
+    for (int w2 = 0; w2 < RED_THREADS / 32; ++w2) {
+      t += so[w2];
+      c += sc[w2];
+      z += sz[w2];
+    }
+    a.part_obj[blockIdx.x] = t;
+    a.part_cnt[2 * blockIdx.x] = c;
+    a.part_cnt[2 * blockIdx.x + 1] = z;
+  }
+}
+
+__global__ void k_reduce_final(const ReduceArgs a, int nblocks) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double t = 0.0;
+  unsigned long long c = 0, z = 0;
+  for (int b = 0; b < nblocks; ++b) {
+    t += a.part_obj[b];
+    c += a.part_cnt[2 * b];
+    z += a.part_cnt[2 * b + 1];
+  }
+  a.out_obj[0] = t;
+  a.out_cnt[0] = c;
+  a.out_cnt[1] = z;
+  if (a.n_inst == 1) a.inst_changed[0] = (long long)c;
+  a.acc_entries[0] += a.entries[0];
+  a.acc_rescored[0] += a.n_rescored[0];
+}
+
+template <typename WT>
+const void* assign_fn() {
+  return reinterpret_cast<const void*>(&k_assign<WT>);
+}
+
+const void* assign_fn_for(int storage) {
+  switch (storage) {
+    case ST_F16:
+      return assign_fn<__half>();
+    case ST_BF16:
+      return assign_fn<__nv_bfloat16>();
+    default:
+      return assign_fn<float>();
+  }
+}
+
+}  // namespace
+
+size_t assign_smem_bytes(int tile_cap, int warps) {
+  return (size_t)warps * ((size_t)tile_cap + 2 * CAND_MAX) * sizeof(float);
+}
+
+cudaError_t assign_prepare(int storage, int tile_cap, int warps) {
+  const size_t bytes = assign_smem_bytes(tile_cap, warps);
+  return cudaFuncSetAttribute(assign_fn_for(storage), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps) {
+  int nb = 0;
+  if (assign_prepare(storage, tile_cap, warps) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage), warps * 32,
+                                                    assign_smem_bytes(tile_cap, warps)) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s) {
+  const size_t smem = assign_smem_bytes(a.tile_cap, warps);
+  switch (a.storage) {
+    case ST_F16:
+      k_assign<__half><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+    case ST_BF16:
+      k_assign<__nv_bfloat16><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+    default:
+      k_assign<float><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+  }
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_rescore(const RescoreArgs& a, int blocks, cudaStream_t s) {
+  k_rescore<<<blocks, 256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_reduce(const ReduceArgs& a, int blocks, cudaStream_t s) {
+  k_reduce<<<blocks, RED_THREADS, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  k_reduce_final<<<1, 32, 0, s>>>(a, blocks);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+}  // namespace ivfk

@@ -1,0 +1,1234 @@
+// C ABI of libivfkm (include/ivf.h): context, device layout, autotuner,
+// CUDA-graph iterations.  All arithmetic of the method runs in the kernels of
+// assign.cu, update.cu and radix.cu; this file validates, allocates, copies
+// and launches.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/ivf.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "radix.cuh"
+
+namespace ivfk {
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace ivfk
+
+using namespace ivfk;
+
+namespace {
+
+// Counters the kernels update; one device block, mirrored into pinned host memory.
+struct DevCounters {
+  unsigned long long work;
+  unsigned long long entries;
+  unsigned long long n_rescored;
+  unsigned int n_flagged;
+  unsigned int status;
+  double objective;
+  unsigned long long cnt[2];  // changed, zero-sim
+  long long ivf_e;            // entries of the inverted file last built
+  unsigned long long acc_entries;   // timing window sums
+  unsigned long long acc_rescored;
+};
+
+struct Shape {
+  int tile_cap = 0;   // floats per warp
+  int k_tile = 0;     // clusters per tile
+  int tiled = 0;
+  int warps = 0;
+  int blocks = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, Shape> g_tune_cache;
+
+constexpr int kTileChoices[] = {1024, 2048, 4096, 8192, 16384, 32768};
+constexpr size_t kSmemBudget = 227 * 1024;
+
+}  // namespace
+
+struct ivf_ctx {
+  ivf_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  // sizes
+  int64_t N = 0, nnz = 0, Dt = 0, Kt = 0;
+  int32_t n_inst = 1;
+  int32_t kmax = 0;
+  int tbits = 1, kbits = 1;
+  int64_t cap = 0;  // capacity of means / inverted-file arrays
+  int64_t e_cur = 0;
+  std::vector<int64_t> h_inst_docs, h_inst_toff;
+  std::vector<int32_t> h_inst_clu, h_inst_terms;
+  // allocations
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  // objects
+  int64_t* row_ptr = nullptr;
+  int32_t* term = nullptr;
+  float* val32 = nullptr;
+  void* val_store = nullptr;
+  float* nx = nullptr;
+  int64_t* inst_docs = nullptr;
+  int32_t* inst_clu = nullptr;
+  int64_t* inst_toff = nullptr;
+  int32_t* inst_terms = nullptr;
+  // means, double buffered
+  int64_t* mptr[2] = {nullptr, nullptr};
+  int32_t* mterm[2] = {nullptr, nullptr};
+  double* mval[2] = {nullptr, nullptr};
+  int32_t* mclu[2] = {nullptr, nullptr};
+  int mcur = 0;
+  // inverted file
+  int64_t* term_ptr = nullptr;
+  uint16_t* cid16 = nullptr;
+  int32_t* cid32 = nullptr;
+  void* w = nullptr;
+  int32_t* toff = nullptr;
+  int64_t toff_len = 0;
+  int64_t* d_e = nullptr;  // points into dc
+  // assignment
+  int32_t* assign[2] = {nullptr, nullptr};
+  int alatest = -1;  // buffer holding the latest assignment, -1 = none
+  bool has_prev_for_next = false;
+  float* best = nullptr;
+  float* gap = nullptr;
+  int32_t* flag_obj = nullptr;
+  int32_t* flag_cnt = nullptr;
+  int32_t* flag_cand = nullptr;
+  DevCounters* dc = nullptr;
+  DevCounters* hc = nullptr;  // pinned
+  int red_blocks = 0;
+  double* part_obj = nullptr;
+  unsigned long long* part_cnt = nullptr;
+  long long* inst_changed = nullptr;
+  // members
+  int64_t* cl_ptr = nullptr;
+  int32_t* members = nullptr;
+  double* sum_norm = nullptr;
+  bool members_valid = false;
+  // update scratch
+  uint64_t* k64a = nullptr;
+  uint64_t* k64b = nullptr;
+  uint32_t* v32a = nullptr;
+  uint32_t* v32b = nullptr;
+  uint32_t* flags = nullptr;
+  uint32_t* starts = nullptr;
+  uint64_t* ukey = nullptr;
+  double* usum = nullptr;
+  int64_t* uptr = nullptr;
+  int64_t* newlen = nullptr;
+  int64_t* d_nnz = nullptr;
+  int64_t* d_n = nullptr;
+  int64_t* d_u = nullptr;
+  void* temp = nullptr;
+  int64_t scratch_len = 0;
+  // launch shape
+  Shape shape;
+  bool tuned = false;
+  // state
+  bool means_set = false;
+  int32_t iteration = 0;
+  // graphs keyed by (mcur, alatest)
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  long long graph_kernels[2][2] = {{0, 0}, {0, 0}};
+  bool own_stream = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // timing window: event pool and per-call records
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
+  struct TimedCall {
+    int kind;  // 0 assign (3 events), 1 update (2 events)
+    size_t e0;
+  };
+  std::vector<TimedCall> tcalls;
+};
+
+namespace {
+
+ivf_status fail(ivf_ctx* c, ivf_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+ivf_status fail_cuda(ivf_ctx* c, const char* what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  return fail(c, IVF_E_CUDA, buf);
+}
+
+#define CK(c, expr)                                        \
+  do {                                                     \
+    cudaError_t e_ = (expr);                               \
+    if (e_ != cudaSuccess) return fail_cuda((c), #expr, e_); \
+  } while (0)
+
+#define ST(expr)                     \
+  do {                               \
+    ivf_status s_ = (expr);          \
+    if (s_ != IVF_OK) return s_;     \
+  } while (0)
+
+template <typename T>
+ivf_status dalloc(ivf_ctx* c, T** p, int64_t count) {
+  const size_t bytes = (size_t)std::max<int64_t>(count, 1) * sizeof(T);
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    char buf[256];
+    snprintf(buf, sizeof(buf), "cudaMalloc of %zu bytes failed (%s)", bytes, cudaGetErrorString(e));
+    return fail(c, IVF_E_OOM, buf);
+  }
+  c->allocs.push_back(q);
+  c->bytes += (int64_t)bytes;
+  *p = static_cast<T*>(q);
+  return IVF_OK;
+}
+
+void dfree(ivf_ctx* c, void* p) {
+  if (!p) return;
+  auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+  if (it != c->allocs.end()) {
+    c->allocs.erase(it);
+    cudaFree(p);
+  }
+}
+
+size_t storage_bytes(int st) { return st == IVF_F32 ? 4 : 2; }
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+
+void drop_graphs(ivf_ctx* c) {
+  for (auto& row : c->graph)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+// Means / inverted-file arrays sized for `cap` entries.
+ivf_status alloc_means(ivf_ctx* c, int64_t cap) {
+  for (int b = 0; b < 2; ++b) {
+    dfree(c, c->mterm[b]);
+    dfree(c, c->mval[b]);
+    dfree(c, c->mclu[b]);
+    c->mterm[b] = nullptr;
+    c->mval[b] = nullptr;
+    c->mclu[b] = nullptr;
+  }
+  dfree(c, c->cid16);
+  dfree(c, c->cid32);
+  dfree(c, c->w);
+  c->cid16 = nullptr;
+  c->cid32 = nullptr;
+  c->w = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    ST(dalloc(c, &c->mterm[b], cap));
+    ST(dalloc(c, &c->mval[b], cap));
+    ST(dalloc(c, &c->mclu[b], cap));
+  }
+  ST(dalloc(c, &c->cid16, cap + 8));
+  ST(dalloc(c, &c->cid32, cap));
+  char* wp = nullptr;
+  ST(dalloc(c, &wp, (cap + 8) * (int64_t)storage_bytes(c->cfg.storage)));
+  c->w = wp;
+  c->cap = cap;
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+ivf_status alloc_scratch(ivf_ctx* c, int64_t len) {
+  void* olds[] = {c->k64a, c->k64b, c->v32a, c->v32b, c->temp};
+  for (void* p : olds) dfree(c, p);
+  ST(dalloc(c, &c->k64a, len));
+  ST(dalloc(c, &c->k64b, len));
+  ST(dalloc(c, &c->v32a, len));
+  ST(dalloc(c, &c->v32b, len));
+  size_t tb = std::max({radix_temp_bytes(len), scan_temp_bytes(len + 1), scan_temp_bytes(c->Kt + 1),
+                        scan_temp_bytes(c->Dt + 1)});
+  char* t = nullptr;
+  ST(dalloc(c, &t, (int64_t)tb));
+  c->temp = t;
+  c->scratch_len = len;
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+ivf_status check_status(ivf_ctx* c) {
+  unsigned st = 0;
+  CK(c, cudaMemcpyAsync(&st, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (st) {
+    CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), c->stream));
+    if (st & STS_CAPACITY) return fail(c, IVF_E_OOM, "new means exceed the inverted-file capacity");
+    if (st & STS_BAD_MEANS) return fail(c, IVF_E_INVALID, "a mean row has zero norm, bad or unsorted terms");
+    if (st & STS_BAD_ROWS) return fail(c, IVF_E_INVALID, "object rows failed validation");
+    return fail(c, IVF_E_INVALID, "device status error");
+  }
+  return IVF_OK;
+}
+
+// --------------------------------------------------------------- create
+
+ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vector<int64_t>& inst_docs,
+                         const std::vector<int32_t>& inst_terms, const std::vector<int32_t>& inst_k,
+                         const int64_t* row_ptr, const int32_t* term, const float* val, void* stream,
+                         ivf_ctx** out) {
+  ivf_ctx* c = new ivf_ctx();
+  c->cfg = *cfg;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->n_inst = n_inst;
+  auto bail = [&](ivf_status s) {
+    if (s != IVF_OK && c->err.size()) fprintf(stderr, "libivfkm: %s\n", c->err.c_str());
+    ivf_destroy(c);
+    return s;
+  };
+  if (!c->stream) {
+    // The legacy default stream cannot be captured into a graph: work goes to
+    // a private blocking stream, which the legacy stream orders implicitly.
+    cudaError_t es = cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault);
+    if (es != cudaSuccess) return bail(fail_cuda(c, "cudaStreamCreate", es));
+    c->own_stream = true;
+  }
+  // instance tables
+  c->h_inst_docs = inst_docs;
+  c->h_inst_terms = inst_terms;
+  c->h_inst_clu.assign(n_inst + 1, 0);
+  c->h_inst_toff.assign(n_inst + 1, 0);
+  for (int b = 0; b < n_inst; ++b) {
+    c->h_inst_clu[b + 1] = c->h_inst_clu[b] + inst_k[b];
+    c->h_inst_toff[b + 1] = c->h_inst_toff[b] + inst_terms[b];
+    c->kmax = std::max(c->kmax, inst_k[b]);
+  }
+  c->N = inst_docs[n_inst];
+  c->Kt = c->h_inst_clu[n_inst];
+  c->Dt = c->h_inst_toff[n_inst];
+  c->tbits = bits_for(c->Dt);
+  c->kbits = bits_for(c->Kt);
+  if (c->tbits + c->kbits > 64) return bail(fail(c, IVF_E_UNSUPPORTED, "cluster and term ids need more than 64 bits"));
+  if (c->N >= (int64_t(1) << 31) || c->Kt >= (int64_t(1) << 31) || c->Dt >= (int64_t(1) << 31))
+    return bail(fail(c, IVF_E_UNSUPPORTED, "N, K and D must be below 2^31"));
+
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(fail_cuda(c, "cudaGetDevice", e));
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(fail_cuda(c, "cudaDeviceGetAttribute", e));
+
+  // row_ptr checked on the host
+  std::vector<int64_t> hrp(c->N + 1);
+  e = cudaMemcpy(hrp.data(), row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault);
+  if (e != cudaSuccess) return bail(fail_cuda(c, "copy row_ptr", e));
+  if (hrp[0] != 0) return bail(fail(c, IVF_E_INVALID, "row_ptr[0] must be 0"));
+  for (int64_t i = 0; i < c->N; ++i)
+    if (hrp[i + 1] < hrp[i]) return bail(fail(c, IVF_E_INVALID, "row_ptr must be non-decreasing"));
+  c->nnz = hrp[c->N];
+  if (cfg->nnz >= 0 && n_inst == 1 && cfg->nnz != c->nnz)
+    return bail(fail(c, IVF_E_INVALID, "row_ptr[N] differs from cfg->nnz"));
+  if (c->nnz >= (int64_t(1) << 32) - 2) return bail(fail(c, IVF_E_UNSUPPORTED, "nnz must be below 2^32"));
+  for (int b = 0; b < n_inst; ++b)
+    if (hrp[inst_docs[b + 1]] - hrp[inst_docs[b]] > (int64_t)inst_terms[b] * (inst_docs[b + 1] - inst_docs[b]))
+      return bail(fail(c, IVF_E_INVALID, "more tuples than terms allow"));
+
+  const int64_t N = c->N, nnz = c->nnz;
+  ivf_status s;
+#define AL(p, n)                    \
+  if ((s = dalloc(c, &(p), (n))) != IVF_OK) return bail(s);
+  AL(c->row_ptr, N + 1);
+  AL(c->term, nnz);
+  AL(c->val32, nnz);
+  if (cfg->storage != IVF_F32) {
+    char* vs = nullptr;
+    AL(vs, nnz * 2 + 16);
+    c->val_store = vs;
+  } else {
+    c->val_store = c->val32;
+  }
+  AL(c->nx, N);
+  AL(c->inst_docs, n_inst + 1);
+  AL(c->inst_clu, n_inst + 1);
+  AL(c->inst_toff, n_inst + 1);
+  AL(c->inst_terms, n_inst);
+  for (int b = 0; b < 2; ++b) AL(c->mptr[b], c->Kt + 1);
+  AL(c->term_ptr, c->Dt + 1);
+  for (int b = 0; b < 2; ++b) AL(c->assign[b], N);
+  AL(c->best, N);
+  AL(c->gap, N);
+  AL(c->flag_obj, N);
+  AL(c->flag_cnt, N);
+  AL(c->flag_cand, N * (int64_t)CAND_MAX);
+  AL(c->dc, 1);
+  c->d_e = reinterpret_cast<int64_t*>(&c->dc->ivf_e);
+  c->red_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 4 * (int64_t)c->num_sms);
+  if (c->red_blocks < 1) c->red_blocks = 1;
+  AL(c->part_obj, c->red_blocks);
+  AL(c->part_cnt, 2 * (int64_t)c->red_blocks);
+  AL(c->inst_changed, n_inst);
+  AL(c->cl_ptr, c->Kt + 1);
+  AL(c->members, N);
+  AL(c->sum_norm, c->Kt);
+  AL(c->flags, nnz + 1);
+  AL(c->starts, nnz + 1);
+  AL(c->ukey, nnz);
+  AL(c->usum, nnz);
+  AL(c->uptr, c->Kt + 1);
+  AL(c->newlen, c->Kt + 1);
+  AL(c->d_nnz, 1);
+  AL(c->d_n, 1);
+  AL(c->d_u, 1);
+  // smallest tile gives the longest per-term offset rows
+  const int64_t tiles_max = ceil_div(c->kmax, kTileChoices[0]);
+  c->toff_len = c->Dt * (tiles_max + 1);
+  if (c->kmax > kTileChoices[0]) AL(c->toff, c->toff_len);
+#undef AL
+  e = cudaMallocHost(&c->hc, sizeof(DevCounters));
+  if (e != cudaSuccess) return bail(fail_cuda(c, "cudaMallocHost", e));
+  for (auto& ev : c->ev) {
+    e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return bail(fail_cuda(c, "cudaEventCreate", e));
+  }
+  if ((s = alloc_means(c, nnz + nnz / 4 + 4096)) != IVF_OK) return bail(s);
+  if ((s = alloc_scratch(c, std::max<int64_t>({nnz, c->cap, N, 1}))) != IVF_OK) return bail(s);
+
+  cudaStream_t st = c->stream;
+#define CKB(expr)                                   \
+  do {                                              \
+    cudaError_t e2 = (expr);                        \
+    if (e2 != cudaSuccess) return bail(fail_cuda(c, #expr, e2)); \
+  } while (0)
+  CKB(cudaMemsetAsync(c->dc, 0, sizeof(DevCounters), st));
+  CKB(cudaMemcpyAsync(c->row_ptr, hrp.data(), sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+  CKB(cudaMemcpyAsync(c->term, term, sizeof(int32_t) * nnz, cudaMemcpyDefault, st));
+  CKB(cudaMemcpyAsync(c->val32, val, sizeof(float) * nnz, cudaMemcpyDefault, st));
+  CKB(cudaMemcpyAsync(c->inst_docs, c->h_inst_docs.data(), sizeof(int64_t) * (n_inst + 1), cudaMemcpyHostToDevice, st));
+  CKB(cudaMemcpyAsync(c->inst_clu, c->h_inst_clu.data(), sizeof(int32_t) * (n_inst + 1), cudaMemcpyHostToDevice, st));
+  CKB(cudaMemcpyAsync(c->inst_toff, c->h_inst_toff.data(), sizeof(int64_t) * (n_inst + 1), cudaMemcpyHostToDevice, st));
+  CKB(cudaMemcpyAsync(c->inst_terms, c->h_inst_terms.data(), sizeof(int32_t) * n_inst, cudaMemcpyHostToDevice, st));
+  const int64_t dn[2] = {nnz, N};
+  CKB(cudaMemcpyAsync(c->d_nnz, &dn[0], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CKB(cudaMemcpyAsync(c->d_n, &dn[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  CKB(launch_prepare_objects(N, nnz, 0, c->row_ptr, c->term, c->val32,
+                             cfg->storage == IVF_F32 ? nullptr : c->val_store, cfg->storage, c->nx, n_inst,
+                             c->inst_docs, c->inst_toff, c->inst_terms, (cfg->flags & IVF_FLAG_VALIDATE) ? 1 : 0,
+                             &c->dc->status, st));
+#undef CKB
+  if ((s = check_status(c)) != IVF_OK) return bail(s);
+  *out = c;
+  return IVF_OK;
+}
+
+ivf_status validate_cfg(const ivf_config* cfg) {
+  if (!cfg) return IVF_E_INVALID;
+  if (cfg->storage < IVF_F32 || cfg->storage > IVF_BF16) return IVF_E_INVALID;
+  if (cfg->empty_policy != 0 && cfg->empty_policy != 1) return IVF_E_INVALID;
+  if (cfg->rescore != 0 && cfg->rescore != 1) return IVF_E_INVALID;
+  if (cfg->warps_per_block < 0 || cfg->warps_per_block > 32) return IVF_E_INVALID;
+  if (cfg->k_tile < 0) return IVF_E_INVALID;
+  return IVF_OK;
+}
+
+// ---------------------------------------------------------- inverted file
+
+IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
+  IvfBuildArgs a{};
+  a.kt = c->Kt;
+  a.dt = c->Dt;
+  a.cap = c->cap;
+  a.tbits = c->tbits;
+  a.n_inst = c->n_inst;
+  a.inst_clu = c->inst_clu;
+  a.mptr = c->mptr[mb];
+  a.mterm = c->mterm[mb];
+  a.mval = c->mval[mb];
+  a.mclu = c->mclu[mb];
+  a.term_ptr = c->term_ptr;
+  a.cid16 = c->cid16;
+  a.cid32 = c->cid32;
+  a.w = c->w;
+  a.storage = c->cfg.storage;
+  a.toff = c->shape.tiled ? c->toff : nullptr;
+  a.k_tile = c->shape.k_tile;
+  a.n_tiles_max = c->shape.tiled ? (int32_t)ceil_div(c->kmax, c->shape.k_tile) : 0;
+  a.d_e = c->d_e;
+  a.k32a = reinterpret_cast<uint32_t*>(c->k64a);
+  a.k32b = reinterpret_cast<uint32_t*>(c->k64b);
+  a.v32a = c->v32a;
+  a.v32b = c->v32b;
+  a.temp = c->temp;
+  a.status = &c->dc->status;
+  return a;
+}
+
+// Stream-ordered: rebuild the inverted file from means buffer mb.
+ivf_status enqueue_build_ivf(ivf_ctx* c, int mb) {
+  CK(c, launch_build_ivf(ivf_args(c, mb), c->stream));
+  return IVF_OK;
+}
+
+// ------------------------------------------------------------ autotune
+
+AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
+  AssignArgs a{};
+  a.n_docs = c->N;
+  a.row_ptr = c->row_ptr;
+  a.term = c->term;
+  a.val = c->val_store;
+  a.nx = c->nx;
+  a.n_inst = c->n_inst;
+  a.inst_docs = c->inst_docs;
+  a.inst_clu = c->inst_clu;
+  a.term_ptr = c->term_ptr;
+  a.cid = c->cid16;
+  a.w = c->w;
+  a.toff = sh.tiled ? c->toff : nullptr;
+  a.n_tiles_max = sh.tiled ? (int32_t)ceil_div(c->kmax, sh.k_tile) : 0;
+  a.k_tile = sh.k_tile;
+  a.tiled = sh.tiled;
+  a.tile_cap = sh.tile_cap;
+  a.storage = c->cfg.storage;
+  a.rescore = rescore;
+  a.assign = c->assign[target];
+  a.best = c->best;
+  a.gap = c->gap;
+  a.work = &c->dc->work;
+  a.entries = &c->dc->entries;
+  a.n_flagged = &c->dc->n_flagged;
+  a.flag_obj = c->flag_obj;
+  a.flag_cnt = c->flag_cnt;
+  a.flag_cand = c->flag_cand;
+  return a;
+}
+
+bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out) {
+  Shape sh;
+  if (k_tile <= 0 || k_tile >= c->kmax) {
+    if (c->kmax > 65536) return false;
+    sh.tiled = 0;
+    sh.k_tile = c->kmax;
+    sh.tile_cap = (c->kmax + 3) & ~3;
+  } else {
+    if (!is_pow2(k_tile) || k_tile < 512 || k_tile > 65536) return false;
+    sh.tiled = 1;
+    sh.k_tile = k_tile;
+    sh.tile_cap = k_tile;
+  }
+  const size_t per_warp = ((size_t)sh.tile_cap + 2 * CAND_MAX) * sizeof(float);
+  int wmax = (int)std::min<size_t>(kSmemBudget / per_warp, 16);
+  if (wmax < 1) return false;
+  int warps = warps_req > 0 ? std::min(warps_req, wmax) : std::min(wmax, 8);
+  if (warps_req > 0 && (size_t)warps_req * per_warp > kSmemBudget) return false;
+  sh.warps = warps;
+  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps);
+  if (bps < 1) return false;
+  sh.blocks = bps * c->num_sms;
+  *out = sh;
+  return true;
+}
+
+ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
+  c->shape = sh;
+  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps));
+  if (sh.tiled) {
+    IvfBuildArgs a = ivf_args(c, c->mcur);
+    CK(c, launch_build_toff(a, c->stream));
+  }
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+ivf_status autotune(ivf_ctx* c) {
+  std::vector<Shape> cands;
+  Shape sh;
+  if (c->cfg.k_tile > 0) {
+    if (!shape_for(c, c->cfg.k_tile, c->cfg.warps_per_block, &sh))
+      return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
+    cands.push_back(sh);
+  } else {
+    if (shape_for(c, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+    for (int t : kTileChoices)
+      if (t < c->kmax && shape_for(c, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+  }
+  if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
+  auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12, c->cfg.storage, c->n_inst);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
+      ST(set_shape(c, it->second));
+      c->tuned = true;
+      return IVF_OK;
+    }
+  }
+  if (cands.size() == 1) {
+    ST(set_shape(c, cands[0]));
+    c->tuned = true;
+    return IVF_OK;
+  }
+  // Time one assignment per candidate (no re-score) on the real data.
+  const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
+  float best_ms = 1e30f;
+  Shape best_sh = cands[0];
+  for (const Shape& cand : cands) {
+    ST(set_shape(c, cand));
+    AssignArgs a = assign_args(c, cand, target, 0);
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(c, cudaMemsetAsync(c->dc, 0, sizeof(unsigned long long) * 2, c->stream));
+      CK(c, cudaEventRecord(c->ev[0], c->stream));
+      CK(c, launch_assign(a, cand.warps, cand.blocks, c->stream));
+      CK(c, cudaEventRecord(c->ev[1], c->stream));
+      CK(c, cudaEventSynchronize(c->ev[1]));
+      float ms = 0.f;
+      CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      ms_min = std::min(ms_min, ms);
+    }
+    if (ms_min < best_ms) {
+      best_ms = ms_min;
+      best_sh = cand;
+    }
+  }
+  ST(set_shape(c, best_sh));
+  c->tuned = true;
+  if (c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_sh;
+  }
+  return IVF_OK;
+}
+
+// ------------------------------------------------------ enqueue phases
+
+cudaError_t timing_event(ivf_ctx* c, size_t* idx) {
+  if (c->tev_used == c->tev.size()) {
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    c->tev.push_back(e);
+  }
+  *idx = c->tev_used++;
+  return cudaEventRecord(c->tev[*idx], c->stream);
+}
+
+// Assignment (+ re-score + reductions) into buffer `target`, previous `prev` (-1 none).
+ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) {
+  cudaStream_t s = c->stream;
+  CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), s));
+  CK(c, cudaMemsetAsync(c->inst_changed, 0, sizeof(long long) * c->n_inst, s));
+  AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
+  size_t e0 = 0, e1 = 0, e2 = 0;
+  if (timed) CK(c, timing_event(c, &e0));
+  CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s));
+  if (timed) CK(c, timing_event(c, &e1));
+  if (c->cfg.rescore) {
+    RescoreArgs r{};
+    r.row_ptr = c->row_ptr;
+    r.term = c->term;
+    r.val32 = c->val32;
+    r.n_inst = c->n_inst;
+    r.inst_docs = c->inst_docs;
+    r.inst_clu = c->inst_clu;
+    r.mptr = c->mptr[c->mcur];
+    r.mterm = c->mterm[c->mcur];
+    r.mval = c->mval[c->mcur];
+    r.n_flagged = &c->dc->n_flagged;
+    r.flag_obj = c->flag_obj;
+    r.flag_cnt = c->flag_cnt;
+    r.flag_cand = c->flag_cand;
+    r.assign = c->assign[target];
+    r.best = c->best;
+    r.gap = c->gap;
+    r.n_rescored = &c->dc->n_rescored;
+    CK(c, launch_rescore(r, 2 * c->num_sms, s));
+  }
+  ReduceArgs ra{};
+  ra.n_docs = c->N;
+  ra.assign = c->assign[target];
+  ra.prev = prev >= 0 ? c->assign[prev] : nullptr;
+  ra.best = c->best;
+  ra.n_inst = c->n_inst;
+  ra.inst_docs = c->inst_docs;
+  ra.inst_changed = c->inst_changed;
+  ra.part_obj = c->part_obj;
+  ra.part_cnt = c->part_cnt;
+  ra.out_obj = &c->dc->objective;
+  ra.out_cnt = c->dc->cnt;
+  ra.entries = &c->dc->entries;
+  ra.n_rescored = &c->dc->n_rescored;
+  ra.acc_entries = &c->dc->acc_entries;
+  ra.acc_rescored = &c->dc->acc_rescored;
+  CK(c, launch_reduce(ra, c->red_blocks, s));
+  if (timed) {
+    CK(c, timing_event(c, &e2));
+    (void)e1;
+    (void)e2;
+    c->tcalls.push_back({0, e0});
+  }
+  return IVF_OK;
+}
+
+// Update from assignment buffer `src`: means mcur -> mcur^1, then the inverted file.
+ivf_status enqueue_update(ivf_ctx* c, int src) {
+  const int mo = c->mcur, mn = c->mcur ^ 1;
+  UpdateArgs u{};
+  u.n_docs = c->N;
+  u.nnz = c->nnz;
+  u.n_inst = c->n_inst;
+  u.kt = c->Kt;
+  u.dt = c->Dt;
+  u.tbits = c->tbits;
+  u.kbits = c->kbits;
+  u.row_ptr = c->row_ptr;
+  u.term = c->term;
+  u.val32 = c->val32;
+  u.inst_docs = c->inst_docs;
+  u.inst_clu = c->inst_clu;
+  u.assign = c->assign[src];
+  u.empty_policy = c->cfg.empty_policy;
+  u.mptr_old = c->mptr[mo];
+  u.mterm_old = c->mterm[mo];
+  u.mval_old = c->mval[mo];
+  u.mptr_new = c->mptr[mn];
+  u.mterm_new = c->mterm[mn];
+  u.mval_new = c->mval[mn];
+  u.mclu_new = c->mclu[mn];
+  u.cap = c->cap;
+  u.cl_ptr = c->cl_ptr;
+  u.members = c->members;
+  u.sum_norm = c->sum_norm;
+  u.k64a = c->k64a;
+  u.k64b = c->k64b;
+  u.v32a = c->v32a;
+  u.v32b = c->v32b;
+  u.flags = c->flags;
+  u.starts = c->starts;
+  u.ukey = c->ukey;
+  u.usum = c->usum;
+  u.uptr = c->uptr;
+  u.newlen = c->newlen;
+  u.d_nnz = c->d_nnz;
+  u.d_n = c->d_n;
+  u.d_u = c->d_u;
+  u.temp = c->temp;
+  u.status = &c->dc->status;
+  CK(c, launch_update_means(u, c->stream));
+  ST(enqueue_build_ivf(c, mn));
+  return IVF_OK;
+}
+
+void fill_stats(ivf_ctx* c, ivf_iter_stats* st) {
+  const DevCounters& h = *c->hc;
+  c->e_cur = h.ivf_e;
+  st->n_changed = (int64_t)h.cnt[0];
+  st->n_zero_sim = (int64_t)h.cnt[1];
+  st->entries_visited = (int64_t)h.entries;
+  st->ivf_entries = c->e_cur;
+  st->n_flagged = (int64_t)h.n_flagged;
+  st->n_rescored = (int64_t)h.n_rescored;
+  st->objective = h.objective;
+  st->t_assign_ms = 0.f;
+  st->t_update_ms = 0.f;
+}
+
+ivf_status read_counters(ivf_ctx* c) {
+  CK(c, cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->e_cur = c->hc->ivf_e;
+  return IVF_OK;
+}
+
+ivf_status copy_mean_rows_in(ivf_ctx* c, const int64_t* mean_ptr, std::vector<int64_t>* hp) {
+  hp->resize(c->Kt + 1);
+  CK(c, cudaMemcpy(hp->data(), mean_ptr, sizeof(int64_t) * (c->Kt + 1), cudaMemcpyDefault));
+  if ((*hp)[0] != 0) return fail(c, IVF_E_INVALID, "mean_ptr[0] must be 0");
+  for (int64_t j = 0; j < c->Kt; ++j)
+    if ((*hp)[j + 1] < (*hp)[j]) return fail(c, IVF_E_INVALID, "mean_ptr must be non-decreasing");
+  return IVF_OK;
+}
+
+ivf_status ensure_capacity(ivf_ctx* c, int64_t e0) {
+  if (e0 <= c->cap) return IVF_OK;
+  ST(alloc_means(c, e0 + c->nnz + 4096));
+  ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N, 1})));
+  c->means_set = false;
+  return IVF_OK;
+}
+
+ivf_status finish_set_means(ivf_ctx* c) {
+  ST(check_status(c));
+  // tile offsets need term_ptr, so the first build may precede the shape choice
+  ST(enqueue_build_ivf(c, c->mcur));
+  ST(read_counters(c));
+  ST(check_status(c));
+  c->means_set = true;
+  c->alatest = -1;
+  c->iteration = 0;
+  c->members_valid = false;
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+// One full iteration (assign + update) enqueued on the stream.
+ivf_status enqueue_iteration(ivf_ctx* c, int target, int prev) {
+  ST(enqueue_assign(c, target, prev));
+  ST(enqueue_update(c, target));
+  CK(c, cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+  return IVF_OK;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+
+extern "C" {
+
+const char* ivf_version(void) { return "libivfkm 0.1 (sm_103a)"; }
+
+int64_t ivf_launch_count(void) { return (int64_t)g_launches.load(); }
+
+const char* ivf_last_error(const ivf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void ivf_destroy(ivf_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  for (auto& ev : ctx->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto& ev : ctx->tev) cudaEventDestroy(ev);
+  for (void* p : ctx->allocs) cudaFree(p);
+  if (ctx->hc) cudaFreeHost(ctx->hc);
+  delete ctx;
+}
+
+ivf_status ivf_create(const ivf_config* cfg, const int64_t* row_ptr, const int32_t* term, const float* val,
+                      void* cuda_stream, ivf_ctx** out) {
+  if (!out) return IVF_E_INVALID;
+  *out = nullptr;
+  if (validate_cfg(cfg) != IVF_OK || !row_ptr || (!term && cfg->nnz > 0) || (!val && cfg->nnz > 0))
+    return IVF_E_INVALID;
+  if (cfg->n_docs < 1 || cfg->n_terms < 1 || cfg->k < 1 || cfg->k > cfg->n_docs || cfg->nnz < 0)
+    return IVF_E_INVALID;
+  std::vector<int64_t> docs = {0, cfg->n_docs};
+  std::vector<int32_t> terms = {(int32_t)cfg->n_terms};
+  std::vector<int32_t> ks = {cfg->k};
+  if (cfg->n_terms >= (int64_t(1) << 31)) return IVF_E_UNSUPPORTED;
+  return create_common(cfg, 1, docs, terms, ks, row_ptr, term, val, cuda_stream, out);
+}
+
+ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* inst_docs, const int32_t* inst_terms,
+                       const int32_t* inst_k, const int64_t* row_ptr, const int32_t* term, const float* val,
+                       void* cuda_stream, ivf_ctx** out) {
+  if (!out) return IVF_E_INVALID;
+  *out = nullptr;
+  if (validate_cfg(cfg) != IVF_OK || n_inst < 1 || !inst_docs || !inst_terms || !inst_k || !row_ptr)
+    return IVF_E_INVALID;
+  std::vector<int64_t> docs(n_inst + 1);
+  std::vector<int32_t> terms(n_inst), ks(n_inst);
+  if (cudaMemcpy(docs.data(), inst_docs, sizeof(int64_t) * (n_inst + 1), cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(terms.data(), inst_terms, sizeof(int32_t) * n_inst, cudaMemcpyDefault) != cudaSuccess ||
+      cudaMemcpy(ks.data(), inst_k, sizeof(int32_t) * n_inst, cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return IVF_E_INVALID;
+  }
+  if (docs[0] != 0) return IVF_E_INVALID;
+  for (int b = 0; b < n_inst; ++b) {
+    const int64_t nb = docs[b + 1] - docs[b];
+    if (nb < 1 || terms[b] < 1 || ks[b] < 1 || ks[b] > nb) return IVF_E_INVALID;
+  }
+  ivf_config c2 = *cfg;
+  c2.nnz = -1;
+  return create_common(&c2, n_inst, docs, terms, ks, row_ptr, term, val, cuda_stream, out);
+}
+
+ivf_status ivf_load_objects(ivf_ctx* c, const int64_t* row_ptr, const int32_t* term, const float* val) {
+  if (!c || !row_ptr || (c->nnz > 0 && (!term || !val))) return fail(c, IVF_E_INVALID, "null argument");
+  std::vector<int64_t> hrp(c->N + 1);
+  CK(c, cudaMemcpy(hrp.data(), row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault));
+  if (hrp[0] != 0 || hrp[c->N] != c->nnz) return fail(c, IVF_E_INVALID, "row_ptr must start at 0 and end at nnz");
+  for (int64_t i = 0; i < c->N; ++i)
+    if (hrp[i + 1] < hrp[i]) return fail(c, IVF_E_INVALID, "row_ptr must be non-decreasing");
+  cudaStream_t s = c->stream;
+  CK(c, cudaMemcpyAsync(c->row_ptr, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, s));
+  CK(c, cudaMemcpyAsync(c->term, term, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, s));
+  CK(c, cudaMemcpyAsync(c->val32, val, sizeof(float) * c->nnz, cudaMemcpyDefault, s));
+  CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->val32,
+                               c->cfg.storage == IVF_F32 ? nullptr : c->val_store, c->cfg.storage, c->nx, c->n_inst,
+                               c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
+                               &c->dc->status, s));
+  if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
+  c->members_valid = false;
+  return IVF_OK;
+}
+
+ivf_status ivf_set_means(ivf_ctx* c, const int64_t* mean_ptr, const int32_t* mean_term, const float* mean_val) {
+  if (!c || !mean_ptr) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->n_inst != 1) return fail(c, IVF_E_UNSUPPORTED, "batched contexts take means from documents");
+  std::vector<int64_t> hp;
+  ST(copy_mean_rows_in(c, mean_ptr, &hp));
+  const int64_t e0 = hp[c->Kt];
+  if (e0 > 0 && (!mean_term || !mean_val)) return fail(c, IVF_E_INVALID, "null mean arrays");
+  ST(ensure_capacity(c, e0));
+  const int mb = c->mcur;
+  std::vector<float> hv(e0);
+  std::vector<double> hd(e0);
+  CK(c, cudaMemcpy(hv.data(), mean_val, sizeof(float) * e0, cudaMemcpyDefault));
+  for (int64_t e = 0; e < e0; ++e) hd[e] = (double)hv[e];
+  CK(c, cudaMemcpyAsync(c->mptr[mb], hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->mterm[mb], mean_term, sizeof(int32_t) * e0, cudaMemcpyDefault, c->stream));
+  CK(c, cudaMemcpyAsync(c->mval[mb], hd.data(), sizeof(double) * e0, cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 1,
+                              c->stream));
+  return finish_set_means(c);
+}
+
+ivf_status ivf_restore_means(ivf_ctx* c, const int64_t* ptr, const int32_t* term, const double* val,
+                             int32_t iteration) {
+  if (!c || !ptr) return fail(c, IVF_E_INVALID, "null argument");
+  std::vector<int64_t> hp;
+  ST(copy_mean_rows_in(c, ptr, &hp));
+  const int64_t e0 = hp[c->Kt];
+  if (e0 > 0 && (!term || !val)) return fail(c, IVF_E_INVALID, "null mean arrays");
+  ST(ensure_capacity(c, e0));
+  const int mb = c->mcur;
+  std::vector<int32_t> ht(e0);
+  CK(c, cudaMemcpy(ht.data(), term, sizeof(int32_t) * e0, cudaMemcpyDefault));
+  if (c->n_inst > 1) {  // local -> global term ids
+    for (int64_t j = 0; j < c->Kt; ++j) {
+      int b = (int)(std::upper_bound(c->h_inst_clu.begin(), c->h_inst_clu.end(), (int32_t)j) - c->h_inst_clu.begin()) - 1;
+      for (int64_t e = hp[j]; e < hp[j + 1]; ++e) ht[e] += (int32_t)c->h_inst_toff[b];
+    }
+  }
+  CK(c, cudaMemcpyAsync(c->mptr[mb], hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->mterm[mb], ht.data(), sizeof(int32_t) * e0, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->mval[mb], val, sizeof(double) * e0, cudaMemcpyDefault, c->stream));
+  CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 0,
+                              c->stream));
+  ST(finish_set_means(c));
+  c->iteration = iteration;
+  return IVF_OK;
+}
+
+ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
+  if (!c || !doc_ids) return fail(c, IVF_E_INVALID, "null argument");
+  std::vector<int32_t> ids(c->Kt);
+  CK(c, cudaMemcpy(ids.data(), doc_ids, sizeof(int32_t) * c->Kt, cudaMemcpyDefault));
+  // local -> global object ids; distinct within each instance
+  for (int b = 0; b < c->n_inst; ++b) {
+    const int64_t nb = c->h_inst_docs[b + 1] - c->h_inst_docs[b];
+    std::vector<int32_t> seen(ids.begin() + c->h_inst_clu[b], ids.begin() + c->h_inst_clu[b + 1]);
+    std::sort(seen.begin(), seen.end());
+    for (size_t q = 0; q < seen.size(); ++q) {
+      if (seen[q] < 0 || seen[q] >= nb) return fail(c, IVF_E_INVALID, "doc id out of range");
+      if (q && seen[q] == seen[q - 1]) return fail(c, IVF_E_INVALID, "doc ids must be distinct");
+    }
+    for (int32_t j = c->h_inst_clu[b]; j < c->h_inst_clu[b + 1]; ++j) ids[j] += (int32_t)c->h_inst_docs[b];
+  }
+  // row lengths on the host to size the means
+  std::vector<int64_t> hrp(c->N + 1);
+  CK(c, cudaMemcpy(hrp.data(), c->row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToHost));
+  int64_t e0 = 0;
+  for (int64_t j = 0; j < c->Kt; ++j) e0 += hrp[ids[j] + 1] - hrp[ids[j]];
+  ST(ensure_capacity(c, e0));
+  int32_t* d_ids = reinterpret_cast<int32_t*>(c->flag_obj);  // scratch: Kt <= N
+  const int mb = c->mcur;
+  CK(c, cudaMemcpyAsync(d_ids, ids.data(), sizeof(int32_t) * c->Kt, cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_gather_rows(c->Kt, d_ids, c->row_ptr, c->term, c->val32, c->mptr[mb], c->mterm[mb], c->mval[mb],
+                           c->temp, c->stream, 0));
+  CK(c, launch_gather_rows(c->Kt, d_ids, c->row_ptr, c->term, c->val32, c->mptr[mb], c->mterm[mb], c->mval[mb],
+                           c->temp, c->stream, 1));
+  CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 1,
+                              c->stream));
+  return finish_set_means(c);
+}
+
+ivf_status ivf_assign(ivf_ctx* c, int32_t* assign_out, float* best_out, float* gap_out, ivf_iter_stats* stats_out) {
+  if (!c) return IVF_E_INVALID;
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  if (!c->tuned) ST(autotune(c));
+  const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
+  const int prev = c->alatest;
+  CK(c, cudaEventRecord(c->ev[0], c->stream));
+  ST(enqueue_assign(c, target, prev, c->timing));
+  CK(c, cudaEventRecord(c->ev[1], c->stream));
+  c->alatest = target;
+  if (assign_out)
+    CK(c, cudaMemcpyAsync(assign_out, c->assign[target], sizeof(int32_t) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (best_out) CK(c, cudaMemcpyAsync(best_out, c->best, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (gap_out) CK(c, cudaMemcpyAsync(gap_out, c->gap, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (stats_out) {
+    ST(read_counters(c));
+    fill_stats(c, stats_out);
+    CK(c, cudaEventElapsedTime(&stats_out->t_assign_ms, c->ev[0], c->ev[1]));
+  }
+  return IVF_OK;
+}
+
+ivf_status ivf_update(ivf_ctx* c) {
+  if (!c) return IVF_E_INVALID;
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment to update from");
+  size_t e0 = 0, e1 = 0;
+  if (c->timing) CK(c, timing_event(c, &e0));
+  ST(enqueue_update(c, c->alatest));
+  if (c->timing) {
+    CK(c, timing_event(c, &e1));
+    c->tcalls.push_back({1, e0});
+  }
+  c->mcur ^= 1;
+  c->iteration += 1;
+  c->members_valid = true;
+  return IVF_OK;
+}
+
+ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_t* converged,
+                       ivf_iter_stats* last_stats) {
+  if (!c) return IVF_E_INVALID;
+  if (max_iter < 0) return fail(c, IVF_E_INVALID, "max_iter < 0");
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  if (!c->tuned) ST(autotune(c));
+  int32_t done = 0, conv = 0;
+  const bool use_graph = !(c->cfg.flags & IVF_FLAG_NO_GRAPH);
+  for (int32_t r = 1; r <= max_iter; ++r) {
+    const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
+    const int prev = c->alatest;
+    if (use_graph && prev >= 0) {
+      cudaGraphExec_t& g = c->graph[c->mcur][prev];
+      long long& gk = c->graph_kernels[c->mcur][prev];
+      if (!g) {
+        cudaGraph_t graph = nullptr;
+        const long long before = g_launches.load();
+        CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        ivf_status s = enqueue_iteration(c, target, prev);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+        gk = g_launches.load() - before;
+        g_launches.fetch_sub(gk);  // counted when the graph runs
+        if (s != IVF_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return s;
+        }
+        if (e != cudaSuccess) return fail_cuda(c, "cudaStreamEndCapture", e);
+        e = cudaGraphInstantiate(&g, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          g = nullptr;
+          return fail_cuda(c, "cudaGraphInstantiate", e);
+        }
+      }
+      CK(c, cudaGraphLaunch(g, c->stream));
+      g_launches.fetch_add(gk);
+    } else {
+      ST(enqueue_iteration(c, target, prev));
+    }
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->alatest = target;
+    c->mcur ^= 1;
+    c->iteration += 1;
+    c->members_valid = true;
+    ++done;
+    if (c->hc->status) ST(check_status(c));
+    if (last_stats) fill_stats(c, last_stats);
+    if (r >= 2 && c->hc->cnt[0] == 0) {
+      conv = 1;
+      break;
+    }
+  }
+  if (iters_done) *iters_done = done;
+  if (converged) *converged = conv;
+  return IVF_OK;
+}
+
+ivf_status ivf_get_assign(ivf_ctx* c, int32_t* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment yet");
+  CK(c, cudaMemcpyAsync(out, c->assign[c->alatest], sizeof(int32_t) * c->N, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_best(ivf_ctx* c, float* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment yet");
+  CK(c, cudaMemcpyAsync(out, c->best, sizeof(float) * c->N, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_gap(ivf_ctx* c, float* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment yet");
+  CK(c, cudaMemcpyAsync(out, c->gap, sizeof(float) * c->N, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_info(ivf_ctx* c, ivf_info* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  int64_t e = 0;
+  if (c->means_set) {
+    CK(c, cudaMemcpyAsync(&e, c->mptr[c->mcur] + c->Kt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  }
+  out->n_docs = c->N;
+  out->n_terms = c->Dt;
+  out->nnz = c->nnz;
+  out->k = (int32_t)c->Kt;
+  out->n_instances = c->n_inst;
+  out->ivf_entries = e;
+  out->ivf_capacity = c->cap;
+  out->k_tile = c->shape.k_tile;
+  out->warps_per_block = c->shape.warps;
+  out->iteration = c->iteration;
+  out->storage = c->cfg.storage;
+  out->device_bytes = c->bytes;
+  return IVF_OK;
+}
+
+ivf_status ivf_get_means(ivf_ctx* c, int64_t* ptr, int32_t* term, double* val) {
+  if (!c) return IVF_E_INVALID;
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  const int mb = c->mcur;
+  std::vector<int64_t> hp(c->Kt + 1);
+  CK(c, cudaMemcpyAsync(hp.data(), c->mptr[mb], sizeof(int64_t) * (c->Kt + 1), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const int64_t e = hp[c->Kt];
+  if (ptr) CK(c, cudaMemcpy(ptr, hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyDefault));
+  if (term) {
+    std::vector<int32_t> ht(e);
+    CK(c, cudaMemcpy(ht.data(), c->mterm[mb], sizeof(int32_t) * e, cudaMemcpyDeviceToHost));
+    if (c->n_inst > 1) {
+      for (int64_t j = 0; j < c->Kt; ++j) {
+        int b = (int)(std::upper_bound(c->h_inst_clu.begin(), c->h_inst_clu.end(), (int32_t)j) - c->h_inst_clu.begin()) - 1;
+        for (int64_t q = hp[j]; q < hp[j + 1]; ++q) ht[q] -= (int32_t)c->h_inst_toff[b];
+      }
+    }
+    CK(c, cudaMemcpy(term, ht.data(), sizeof(int32_t) * e, cudaMemcpyDefault));
+  }
+  if (val) CK(c, cudaMemcpy(val, c->mval[mb], sizeof(double) * e, cudaMemcpyDefault));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_inverted_file(ivf_ctx* c, int64_t* term_ptr, int32_t* cid, float* w) {
+  if (!c) return IVF_E_INVALID;
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  CK(c, cudaStreamSynchronize(c->stream));
+  int64_t e = 0;
+  CK(c, cudaMemcpy(&e, c->term_ptr + c->Dt, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (term_ptr) CK(c, cudaMemcpy(term_ptr, c->term_ptr, sizeof(int64_t) * (c->Dt + 1), cudaMemcpyDefault));
+  if (cid) CK(c, cudaMemcpy(cid, c->cid32, sizeof(int32_t) * e, cudaMemcpyDefault));
+  if (w) {
+    std::vector<float> hw(e);
+    if (c->cfg.storage == IVF_F32) {
+      CK(c, cudaMemcpy(hw.data(), c->w, sizeof(float) * e, cudaMemcpyDeviceToHost));
+    } else {
+      std::vector<uint16_t> raw(e);
+      CK(c, cudaMemcpy(raw.data(), c->w, sizeof(uint16_t) * e, cudaMemcpyDeviceToHost));
+      for (int64_t q = 0; q < e; ++q) {
+        if (c->cfg.storage == IVF_F16) {
+          __half_raw hr;
+          hr.x = raw[q];
+          hw[q] = __half2float(__half(hr));
+        } else {
+          uint32_t bits = (uint32_t)raw[q] << 16;
+          float f;
+          memcpy(&f, &bits, 4);
+          hw[q] = f;
+        }
+      }
+    }
+    CK(c, cudaMemcpy(w, hw.data(), sizeof(float) * e, cudaMemcpyDefault));
+  }
+  return IVF_OK;
+}
+
+ivf_status ivf_get_members(ivf_ctx* c, int64_t* cl_ptr, int32_t* members) {
+  if (!c) return IVF_E_INVALID;
+  if (!c->members_valid) return fail(c, IVF_E_STATE, "no update has run since the last change");
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (cl_ptr) CK(c, cudaMemcpy(cl_ptr, c->cl_ptr, sizeof(int64_t) * (c->Kt + 1), cudaMemcpyDefault));
+  if (members) {
+    if (c->n_inst == 1) {
+      CK(c, cudaMemcpy(members, c->members, sizeof(int32_t) * c->N, cudaMemcpyDefault));
+    } else {
+      std::vector<int32_t> hm(c->N);
+      std::vector<int64_t> hcl(c->Kt + 1);
+      CK(c, cudaMemcpy(hm.data(), c->members, sizeof(int32_t) * c->N, cudaMemcpyDeviceToHost));
+      CK(c, cudaMemcpy(hcl.data(), c->cl_ptr, sizeof(int64_t) * (c->Kt + 1), cudaMemcpyDeviceToHost));
+      for (int b = 0; b < c->n_inst; ++b)
+        for (int64_t q = hcl[c->h_inst_clu[b]]; q < hcl[c->h_inst_clu[b + 1]]; ++q)
+          hm[q] -= (int32_t)c->h_inst_docs[b];
+      CK(c, cudaMemcpy(members, hm.data(), sizeof(int32_t) * c->N, cudaMemcpyDefault));
+    }
+  }
+  return IVF_OK;
+}
+
+ivf_status ivf_set_assign(ivf_ctx* c, const int32_t* assign) {
+  if (!c || !assign) return fail(c, IVF_E_INVALID, "null argument");
+  std::vector<int32_t> h(c->N);
+  CK(c, cudaMemcpy(h.data(), assign, sizeof(int32_t) * c->N, cudaMemcpyDefault));
+  for (int b = 0; b < c->n_inst; ++b) {
+    const int32_t kb = c->h_inst_clu[b + 1] - c->h_inst_clu[b];
+    for (int64_t i = c->h_inst_docs[b]; i < c->h_inst_docs[b + 1]; ++i)
+      if (h[i] < 0 || h[i] >= kb) return fail(c, IVF_E_INVALID, "assignment out of range");
+  }
+  const int target = c->alatest < 0 ? 0 : c->alatest;
+  CK(c, cudaMemcpyAsync(c->assign[target], h.data(), sizeof(int32_t) * c->N, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->alatest = target;
+  return IVF_OK;
+}
+
+ivf_status ivf_timing_reset(ivf_ctx* c, int32_t enable) {
+  if (!c) return IVF_E_INVALID;
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->tev_used = 0;
+  c->tcalls.clear();
+  c->timing = enable != 0;
+  CK(c, cudaMemsetAsync(&c->dc->acc_entries, 0, 2 * sizeof(unsigned long long), c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_timing(ivf_ctx* c, ivf_timing* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  ST(read_counters(c));
+  memset(out, 0, sizeof(*out));
+  for (const auto& tc : c->tcalls) {
+    float ms = 0.f;
+    if (tc.kind == 0) {
+      CK(c, cudaEventElapsedTime(&ms, c->tev[tc.e0], c->tev[tc.e0 + 1]));
+      out->assign_kernel_ms += ms;
+      CK(c, cudaEventElapsedTime(&ms, c->tev[tc.e0], c->tev[tc.e0 + 2]));
+      out->assign_step_ms += ms;
+      out->n_assign += 1;
+    } else {
+      CK(c, cudaEventElapsedTime(&ms, c->tev[tc.e0], c->tev[tc.e0 + 1]));
+      out->update_ms += ms;
+      out->n_update += 1;
+    }
+  }
+  out->entries_visited = (int64_t)c->hc->acc_entries;
+  out->n_rescored = (int64_t)c->hc->acc_rescored;
+  return IVF_OK;
+}
+
+ivf_status ivfb_get_changed(ivf_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  CK(c, cudaMemcpyAsync(out, c->inst_changed, sizeof(int64_t) * c->n_inst, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+}  // extern "C"

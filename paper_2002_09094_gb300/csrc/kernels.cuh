@@ -1,0 +1,192 @@
+// Internal launch interface between the C ABI (ivf_api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ivfk {
+
+enum Storage : int { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+
+// Candidate clusters kept per flagged object for the FP64 re-score.
+constexpr int CAND_MAX = 32;
+
+// Device status word bits (ctx->d_status).
+enum StatusBits : unsigned {
+  STS_CAPACITY = 1u,   // the new means did not fit the inverted-file capacity
+  STS_BAD_MEANS = 2u,  // a mean row given by the caller has zero norm or bad terms
+  STS_BAD_ROWS = 4u,   // object rows failed validation
+};
+
+// Everything the assignment kernel reads and writes.
+struct AssignArgs {
+  int64_t n_docs;
+  const int64_t* row_ptr;  // [N+1]
+  const int32_t* term;     // [nnz] global term ids
+  const void* val;         // [nnz] storage type
+  const float* nx;         // [N] object norm, rounded up
+  int32_t n_inst;
+  const int64_t* inst_docs;  // [n_inst+1]
+  const int32_t* inst_clu;   // [n_inst+1]
+  const int64_t* term_ptr;   // [D+1]
+  const uint16_t* cid;       // [E] local cluster id & 0xFFFF
+  const void* w;             // [E] storage type
+  const int32_t* toff;       // [D * (n_tiles_max+1)] per (term, tile) offset inside the list, or null
+  int32_t n_tiles_max;
+  int32_t k_tile;            // clusters per tile (power of two when tiled)
+  int32_t tiled;
+  int32_t tile_cap;          // floats of accumulator per warp (multiple of 4)
+  int32_t storage;
+  int32_t rescore;
+  int32_t* assign;           // [N]
+  float* best;               // [N]
+  float* gap;                // [N]
+  unsigned long long* work;     // object counter, zero before launch
+  unsigned long long* entries;  // visited posting entries (accumulated)
+  unsigned int* n_flagged;      // flagged objects (accumulated from 0)
+  int32_t* flag_obj;            // [N]
+  int32_t* flag_cnt;            // [N] candidates, -1 = overflow (all clusters)
+  int32_t* flag_cand;           // [N * CAND_MAX]
+};
+
+size_t assign_smem_bytes(int tile_cap, int warps);
+cudaError_t assign_prepare(int storage, int tile_cap, int warps);
+cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s);
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps);
+
+struct RescoreArgs {
+  const int64_t* row_ptr;
+  const int32_t* term;
+  const float* val32;
+  int32_t n_inst;
+  const int64_t* inst_docs;
+  const int32_t* inst_clu;
+  const int64_t* mptr;   // [Kt+1] cluster-major FP64 means
+  const int32_t* mterm;  // global term ids
+  const double* mval;
+  const unsigned int* n_flagged;
+  const int32_t* flag_obj;
+  const int32_t* flag_cnt;
+  const int32_t* flag_cand;
+  int32_t* assign;
+  float* best;
+  float* gap;
+  unsigned long long* n_rescored;
+};
+cudaError_t launch_rescore(const RescoreArgs& a, int blocks, cudaStream_t s);
+
+struct ReduceArgs {
+  int64_t n_docs;
+  const int32_t* assign;
+  const int32_t* prev;   // null on the first assignment
+  const float* best;
+  int32_t n_inst;
+  const int64_t* inst_docs;
+  long long* inst_changed;  // [n_inst], zeroed before launch
+  double* part_obj;         // [blocks]
+  unsigned long long* part_cnt;  // [2 * blocks]: changed, zero-sim
+  double* out_obj;          // [1]
+  unsigned long long* out_cnt;   // [2]
+  // window accumulators (added to by the final reduction)
+  const unsigned long long* entries;
+  const unsigned long long* n_rescored;
+  unsigned long long* acc_entries;
+  unsigned long long* acc_rescored;
+};
+cudaError_t launch_reduce(const ReduceArgs& a, int blocks, cudaStream_t s);
+
+// ---------------------------------------------------------------- update
+struct UpdateArgs {
+  int64_t n_docs, nnz;
+  int32_t n_inst;
+  int64_t kt;   // total clusters
+  int64_t dt;   // total terms
+  int tbits, kbits;
+  const int64_t* row_ptr;
+  const int32_t* term;
+  const float* val32;
+  const int64_t* inst_docs;
+  const int32_t* inst_clu;
+  const int32_t* assign;  // local cluster ids
+  int32_t empty_policy;
+  // old and new cluster-major means
+  const int64_t* mptr_old;
+  const int32_t* mterm_old;
+  const double* mval_old;
+  int64_t* mptr_new;
+  int32_t* mterm_new;
+  double* mval_new;
+  int32_t* mclu_new;
+  int64_t cap;  // capacity of the means / inverted file arrays
+  // members (C_j)
+  int64_t* cl_ptr;      // [Kt+1]
+  int32_t* members;     // [N]
+  double* sum_norm;     // [Kt]
+  // scratch
+  uint64_t* k64a;
+  uint64_t* k64b;
+  uint32_t* v32a;
+  uint32_t* v32b;
+  uint32_t* flags;      // [nnz+1]
+  uint32_t* starts;     // [nnz+1]
+  uint64_t* ukey;       // [nnz]
+  double* usum;         // [nnz]
+  int64_t* uptr;        // [Kt+1]
+  int64_t* newlen;      // [Kt+1]
+  int64_t* d_nnz;       // device copy of nnz
+  int64_t* d_n;         // device copy of N
+  int64_t* d_u;         // number of unique (cluster, term) keys
+  void* temp;           // radix / scan scratch
+  unsigned* status;
+};
+cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s);
+
+struct IvfBuildArgs {
+  int64_t kt, dt, cap;
+  int tbits;
+  int32_t n_inst;
+  const int32_t* inst_clu;
+  const int64_t* mptr;   // [Kt+1]; mptr[Kt] = E
+  const int32_t* mterm;
+  const double* mval;
+  const int32_t* mclu;
+  int64_t* term_ptr;     // [Dt+1]
+  uint16_t* cid16;
+  int32_t* cid32;
+  void* w;               // storage type
+  int32_t storage;
+  int32_t* toff;         // or null
+  int32_t n_tiles_max, k_tile;
+  int64_t* d_e;          // [1] receives E
+  // scratch
+  uint32_t* k32a;
+  uint32_t* k32b;
+  uint32_t* v32a;
+  uint32_t* v32b;
+  void* temp;
+  unsigned* status;
+};
+cudaError_t launch_build_ivf(const IvfBuildArgs& a, cudaStream_t s);
+cudaError_t launch_build_toff(const IvfBuildArgs& a, cudaStream_t s);
+
+// Means from rows: validate cluster-major rows, fill the row owner of every
+// entry and (normalise != 0) divide each row by its FP64 L2 norm in place;
+// a zero-norm row (when normalising) or a bad term sets STS_BAD_MEANS.
+cudaError_t launch_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu,
+                                  int64_t dt, const int32_t* mterm, unsigned* status, int normalise,
+                                  cudaStream_t s);
+// Gather object rows d_ids[j] (global object ids) as mean rows (values promoted to FP64).
+cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t* row_ptr,
+                               const int32_t* term, const float* val32, int64_t* lens_then_ptr,
+                               int32_t* mterm, double* mval, void* temp, cudaStream_t s, int phase);
+
+// Object-side preparation: norms, storage copy, global term ids, validation.
+cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local_max, const int64_t* row_ptr,
+                                   int32_t* term, const float* val32, void* val_store, int storage,
+                                   float* nx, int32_t n_inst, const int64_t* inst_docs,
+                                   const int64_t* inst_toff, const int32_t* inst_terms, int validate,
+                                   unsigned* status, cudaStream_t s);
+
+cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
+
+}  // namespace ivfk

@@ -1,0 +1,33 @@
+// Device-wide exclusive scan and stable LSD radix sort (key, uint32 payload).
+//
+// These are the counting-sort and prefix-sum building blocks of the update
+// step: grouping objects by cluster (the sets C_j of Algorithm 3), merging
+// member terms per cluster, and the term-major rebuild of the inverted file
+// (Section 3: each posting list xi_s ascends in cluster id because a stable
+// sort by term keeps the cluster-major input order).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ivfk {
+
+// Exclusive scan of n values into out[0..n]; out[n] receives the total.
+// in and out may be the same array (out must hold n+1 values).
+size_t scan_temp_bytes(int64_t n);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t s);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
+
+// Stable LSD radix sort of d_n[0] (<= n_max) pairs, 8 bits per pass over the
+// low `bits` bits of the key.  Buffers ping-pong between (keys, vals) and
+// (keys_alt, vals_alt); *in_alt reports where the result ends up (a function
+// of `bits` only, so it is the same at every graph replay).
+size_t radix_temp_bytes(int64_t n_max);
+cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                           const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
+                           bool* in_alt);
+cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                           const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
+                           bool* in_alt);
+
+}  // namespace ivfk

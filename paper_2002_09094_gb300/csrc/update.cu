@@ -1,0 +1,501 @@
+// Update step of Algorithm 3 (IVF) on sm_103a, plus the inverted-file build
+// shared with the initial means.
+//
+// The paper's update fills a dense w in R^D per cluster, divides by |C_j|,
+// and appends (j, w_p / ||w||) to posting list p for every w_p != 0, visiting
+// clusters in ascending j.  Here the same result is produced without a dense
+// K x D array:
+//   A5 group objects by cluster: stable radix sort of (cluster, object);
+//   A6 member sums: every (term, value) of object i gets the key
+//      (cluster(i), term); a stable LSD radix sort brings equal keys together
+//      in ascending object id, and each run is summed sequentially in FP64
+//      (the same order in which the oracle's dense accumulation adds them);
+//   A7 normalise: ||s_j|| accumulated in ascending term order (separate
+//      multiply and add, no contraction), zero sums dropped (w_p != 0),
+//      empty clusters keep their previous mean or become empty;
+//   A8 inverted file: a stable radix sort by term of the cluster-major means
+//      gives posting lists in ascending cluster id; term_ptr by binary search.
+// Dividing by |C_j| before normalising only rescales, so it is skipped.
+#include "common.cuh"
+#include "kernels.cuh"
+#include "radix.cuh"
+
+namespace ivfk {
+
+namespace {
+
+constexpr int T256 = 256;
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
+  int64_t g = ceil_div(n < 1 ? 1 : n, threads);
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+__device__ __forceinline__ int find_inst32(const int32_t* offs, int n_inst, int64_t x) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)offs[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int find_inst64(const int64_t* offs, int n_inst, int64_t x) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename K>
+__device__ __forceinline__ int64_t lower_bound_dev(const K* a, int64_t n, K x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------- A5 members
+
+__global__ void k_member_keys(UpdateArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_docs; i += stride) {
+    const int b = a.n_inst > 1 ? find_inst64(a.inst_docs, a.n_inst, i) : 0;
+    a.v32a[i] = (uint32_t)i;
+    reinterpret_cast<uint32_t*>(a.k64a)[i] = (uint32_t)(a.inst_clu[b] + a.assign[i]);
+  }
+}
+
+__global__ void k_member_out(UpdateArgs a, const uint32_t* keys, const uint32_t* vals) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_docs; i += stride)
+    a.members[i] = (int32_t)vals[i];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= a.kt; j += stride)
+    a.cl_ptr[j] = lower_bound_dev<uint32_t>(keys, a.n_docs, (uint32_t)j);
+}
+
+// ------------------------------------------------------- A6 member sums
+
+// One warp per object: key (global cluster, global term), payload FP32 bits.
+__global__ void k_expand(UpdateArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < a.n_docs; i += nw) {
+    const int b = a.n_inst > 1 ? find_inst64(a.inst_docs, a.n_inst, i) : 0;
+    const uint64_t gc = (uint64_t)(a.inst_clu[b] + a.assign[i]);
+    const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
+    for (int64_t h = r0 + lane; h < r1; h += 32) {
+      a.k64a[h] = (gc << a.tbits) | (uint64_t)(uint32_t)a.term[h];
+      a.v32a[h] = __float_as_uint(a.val32[h]);
+    }
+  }
+}
+
+// After the scan, scanned[e+1] != scanned[e] marks the first entry of a run.
+__global__ void k_heads(const uint64_t* keys, const int64_t* d_n, uint32_t* flags) {
+  const int64_t n = *d_n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    flags[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
+}
+
+__global__ void k_starts(const uint32_t* scanned, const int64_t* d_n, uint32_t* starts, int64_t* d_u) {
+  const int64_t n = *d_n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    if (scanned[e + 1] != scanned[e]) starts[scanned[e]] = (uint32_t)e;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    starts[scanned[n]] = (uint32_t)n;
+    *d_u = (int64_t)scanned[n];
+  }
+}
+
+// Each run of equal keys summed in FP64 in its (ascending object) order.
+__global__ void k_segsum(const uint64_t* keys, const uint32_t* vals, const uint32_t* starts, const int64_t* d_u,
+                         uint64_t* ukey, double* usum) {
+  const int64_t u_n = *d_u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
+    const uint32_t s0 = starts[u], s1 = starts[u + 1];
+    double s = 0.0;
+    for (uint32_t e = s0; e < s1; ++e) s = __dadd_rn(s, (double)__uint_as_float(vals[e]));
+    ukey[u] = keys[s0];
+    usum[u] = s;
+  }
+}
+
+// ------------------------------------------------------------ A7 normalise
+
+__global__ void k_uptr(UpdateArgs a) {
+  const int64_t u_n = *a.d_u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j <= a.kt; j += stride)
+    a.uptr[j] = lower_bound_dev<uint64_t>(a.ukey, u_n, (uint64_t)j << a.tbits);
+}
+
+// Thread per cluster: ||s_j||^2 in ascending term order, count of nonzero
+// elements, and the length of the new mean row.
+__global__ void k_cluster_norm(UpdateArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.kt; j += stride) {
+    double n2 = 0.0;
+    int64_t nz = 0;
+    for (int64_t u = a.uptr[j]; u < a.uptr[j + 1]; ++u) {
+      const double s = a.usum[u];
+      n2 = __dadd_rn(n2, __dmul_rn(s, s));
+      nz += (s != 0.0) ? 1 : 0;
+    }
+    const double nrm = __dsqrt_rn(n2);
+    a.sum_norm[j] = nrm;
+    int64_t len;
+    if (nrm > 0.0)
+      len = nz;
+    else
+      len = a.empty_policy == 0 ? (a.mptr_old[j + 1] - a.mptr_old[j]) : 0;
+    a.newlen[j] = len;
+  }
+}
+
+// Warp per cluster: write mu_j = s_j / ||s_j|| (nonzero elements, in term
+// order) or the kept previous row.
+__global__ void k_write_means(UpdateArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t e_new = a.mptr_new[a.kt];
+  if (e_new > a.cap) {
+    if (gw == 0 && lane == 0) atomicOr(a.status, (unsigned)STS_CAPACITY);
+    return;
+  }
+  const uint64_t tmask = (a.tbits >= 64) ? ~0ull : ((1ull << a.tbits) - 1ull);
+  const unsigned lt = (1u << lane) - 1u;
+  for (int64_t j = gw; j < a.kt; j += nw) {
+    const double nrm = a.sum_norm[j];
+    int64_t dst = a.mptr_new[j];
+    if (nrm > 0.0) {
+      const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
+      for (int64_t ub = u0; ub < u1; ub += 32) {
+        const int64_t u = ub + lane;
+        double s = 0.0;
+        if (u < u1) s = a.usum[u];
+        const bool keep = (u < u1) && (s != 0.0);
+        const unsigned km = __ballot_sync(IVF_FULL_MASK, keep);
+        if (keep) {
+          const int64_t o = dst + __popc(km & lt);
+          a.mterm_new[o] = (int32_t)(a.ukey[u] & tmask);
+          a.mval_new[o] = __ddiv_rn(s, nrm);
+          a.mclu_new[o] = (int32_t)j;
+        }
+        dst += __popc(km);
+      }
+    } else if (a.empty_policy == 0) {
+      const int64_t o0 = a.mptr_old[j], o1 = a.mptr_old[j + 1];
+      for (int64_t q = lane; q < o1 - o0; q += 32) {
+        a.mterm_new[dst + q] = a.mterm_old[o0 + q];
+        a.mval_new[dst + q] = a.mval_old[o0 + q];
+        a.mclu_new[dst + q] = (int32_t)j;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------- A8 inverted file
+
+__global__ void k_ivf_keys(IvfBuildArgs a) {
+  const int64_t e_n = a.mptr[a.kt];
+  const int64_t n = e_n > a.cap ? 0 : e_n;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_e = n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    a.k32a[e] = (uint32_t)a.mterm[e];
+    a.v32a[e] = (uint32_t)e;
+  }
+}
+
+__global__ void k_term_ptr(IvfBuildArgs a, const uint32_t* sorted_terms) {
+  const int64_t n = *a.d_e;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= a.dt; p += stride)
+    a.term_ptr[p] = lower_bound_dev<uint32_t>(sorted_terms, n, (uint32_t)p);
+}
+
+template <typename WT>
+__global__ void k_ivf_fill(IvfBuildArgs a, const uint32_t* perm) {
+  const int64_t n = *a.d_e;
+  WT* w = static_cast<WT*>(a.w);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
+    const uint32_t e = perm[q];
+    const int32_t gc = a.mclu[e];
+    const int b = a.n_inst > 1 ? find_inst32(a.inst_clu, a.n_inst, gc) : 0;
+    const int32_t local = gc - a.inst_clu[b];
+    a.cid32[q] = local;
+    a.cid16[q] = (uint16_t)(local & 0xFFFF);
+    w[q] = from_f64<WT>(a.mval[e]);
+  }
+}
+
+// Per (term, tile): offset inside the term's list of the first entry whose
+// cluster id reaches tile * k_tile.
+__global__ void k_toff(IvfBuildArgs a) {
+  const int64_t per = (int64_t)a.n_tiles_max + 1;
+  const int64_t total = a.dt * per;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += stride) {
+    const int64_t p = x / per;
+    const int64_t tt = x - p * per;
+    const int64_t tb = a.term_ptr[p], te = a.term_ptr[p + 1];
+    const int64_t target = tt * (int64_t)a.k_tile;
+    int64_t lo = tb, hi = te;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)a.cid32[mid] < target)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    a.toff[x] = (int32_t)(lo - tb);
+  }
+}
+
+// ------------------------------------------------------ means from rows
+
+__global__ void k_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu, int64_t dt,
+                                 const int32_t* mterm, unsigned* status, int normalise) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kt; j += stride) {
+    const int64_t r0 = mptr[j], r1 = mptr[j + 1];
+    double n2 = 0.0;
+    bool ok = r1 >= r0;
+    for (int64_t e = r0; e < r1; ++e) {
+      const double v = mval[e];
+      n2 = __dadd_rn(n2, __dmul_rn(v, v));
+      const int32_t t = mterm[e];
+      if (t < 0 || (int64_t)t >= dt || (e > r0 && mterm[e - 1] >= t) || !isfinite(v)) ok = false;
+    }
+    if ((normalise && !(n2 > 0.0)) || !isfinite(n2) || !ok) {
+      atomicOr(status, (unsigned)STS_BAD_MEANS);
+      continue;
+    }
+    const double nrm = __dsqrt_rn(n2);
+    for (int64_t e = r0; e < r1; ++e) {
+      if (normalise) mval[e] = __ddiv_rn(mval[e], nrm);
+      mclu[e] = (int32_t)j;
+    }
+  }
+}
+
+__global__ void k_gather_lens(int64_t kt, const int32_t* doc_ids, const int64_t* row_ptr, int64_t* lens) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kt; j += stride) {
+    const int64_t d = doc_ids[j];
+    lens[j] = row_ptr[d + 1] - row_ptr[d];
+  }
+}
+
+__global__ void k_gather_copy(int64_t kt, const int32_t* doc_ids, const int64_t* row_ptr, const int32_t* term,
+                              const float* val32, const int64_t* mptr, int32_t* mterm, double* mval) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = gw; j < kt; j += nw) {
+    const int64_t d = doc_ids[j];
+    const int64_t r0 = row_ptr[d], len = row_ptr[d + 1] - r0, o = mptr[j];
+    for (int64_t q = lane; q < len; q += 32) {
+      mterm[o + q] = term[r0 + q];
+      mval[o + q] = (double)val32[r0 + q];
+    }
+  }
+}
+
+// --------------------------------------------------------- objects
+
+template <typename WT>
+__global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_t* term, const float* val32,
+                                  WT* val_store, float* nx, int32_t n_inst, const int64_t* inst_docs,
+                                  const int64_t* inst_toff, const int32_t* inst_terms, int validate,
+                                  unsigned* status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = gw; i < n_docs; i += nw) {
+    const int b = n_inst > 1 ? find_inst64(inst_docs, n_inst, i) : 0;
+    const int64_t toff = inst_toff[b];
+    const int32_t d_local = inst_terms[b];
+    const int64_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
+    double ss = 0.0;
+    bool bad = r1 < r0;
+    for (int64_t h = r0 + lane; h < r1; h += 32) {
+      const int32_t t = term[h];
+      const float v = val32[h];
+      if (validate) {
+        if (t < 0 || t >= d_local || !isfinite(v)) bad = true;
+        if (h > r0 && term[h - 1] >= t) bad = true;
+      }
+      ss += (double)v * (double)v;
+      if (val_store) val_store[h] = from_f32<WT>(v);
+    }
+    __syncwarp();
+    if (toff != 0)
+      for (int64_t h = r0 + lane; h < r1; h += 32) term[h] = (int32_t)(term[h] + toff);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(IVF_FULL_MASK, ss, o);
+    const bool any_bad = __any_sync(IVF_FULL_MASK, bad);
+    if (lane == 0) {
+      // an upper bound on ||x_i||: the FP64 sum is within a few ulps, then round up
+      nx[i] = __double2float_ru(__dsqrt_ru(ss * (1.0 + 1e-12)));
+      if (any_bad) atomicOr(status, (unsigned)STS_BAD_ROWS);
+    }
+  }
+}
+
+__global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
+}
+
+}  // namespace
+
+cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
+  const unsigned gN = grid_for(a.n_docs, T256, 8192);
+  // A5: C_j as a stable counting sort of objects by cluster
+  k_member_keys<<<gN, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  {
+    uint32_t* ka = reinterpret_cast<uint32_t*>(a.k64a);
+    uint32_t* kb = reinterpret_cast<uint32_t*>(a.k64b);
+    bool alt = false;
+    IVF_CU(radix_sort_u32(ka, kb, a.v32a, a.v32b, a.d_n, a.n_docs, a.kbits, a.temp, s, &alt));
+    k_member_out<<<grid_for(a.n_docs > a.kt ? a.n_docs : a.kt + 1, T256, 8192), T256, 0, s>>>(
+        a, alt ? kb : ka, alt ? a.v32b : a.v32a);
+    IVF_LAUNCH_CHECK();
+  }
+  // A6: (cluster, term) keys in object order, stable sort, FP64 run sums
+  k_expand<<<grid_for(a.n_docs * 32, T256, 16384), T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  bool alt = false;
+  IVF_CU(radix_sort_u64(a.k64a, a.k64b, a.v32a, a.v32b, a.d_nnz, a.nnz, a.kbits + a.tbits, a.temp, s, &alt));
+  const uint64_t* keys = alt ? a.k64b : a.k64a;
+  const uint32_t* vals = alt ? a.v32b : a.v32a;
+  const unsigned gE = grid_for(a.nnz, T256, 16384);
+  k_heads<<<gE, T256, 0, s>>>(keys, a.d_nnz, a.flags);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_u32(a.flags, a.flags, a.nnz, a.temp, s));
+  k_starts<<<gE, T256, 0, s>>>(a.flags, a.d_nnz, a.starts, a.d_u);
+  IVF_LAUNCH_CHECK();
+  k_segsum<<<gE, T256, 0, s>>>(keys, vals, a.starts, a.d_u, a.ukey, a.usum);
+  IVF_LAUNCH_CHECK();
+  // A7: norms, new row lengths, prefix sums, write
+  const unsigned gK = grid_for(a.kt + 1, T256, 8192);
+  k_uptr<<<gK, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  k_cluster_norm<<<grid_for(a.kt, 64, 8192), 64, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
+  k_write_means<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_build_ivf(const IvfBuildArgs& a, cudaStream_t s) {
+  const unsigned gE = grid_for(a.cap, T256, 16384);
+  k_ivf_keys<<<gE, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  bool alt = false;
+  IVF_CU(radix_sort_u32(a.k32a, a.k32b, a.v32a, a.v32b, a.d_e, a.cap, a.tbits, a.temp, s, &alt));
+  const uint32_t* terms = alt ? a.k32b : a.k32a;
+  const uint32_t* perm = alt ? a.v32b : a.v32a;
+  k_term_ptr<<<grid_for(a.dt + 1, T256, 16384), T256, 0, s>>>(a, terms);
+  IVF_LAUNCH_CHECK();
+  switch (a.storage) {
+    case ST_F16:
+      k_ivf_fill<__half><<<gE, T256, 0, s>>>(a, perm);
+      break;
+    case ST_BF16:
+      k_ivf_fill<__nv_bfloat16><<<gE, T256, 0, s>>>(a, perm);
+      break;
+    default:
+      k_ivf_fill<float><<<gE, T256, 0, s>>>(a, perm);
+      break;
+  }
+  IVF_LAUNCH_CHECK();
+  if (a.toff) IVF_CU(launch_build_toff(a, s));
+  return cudaSuccess;
+}
+
+cudaError_t launch_build_toff(const IvfBuildArgs& a, cudaStream_t s) {
+  k_toff<<<grid_for(a.dt * (a.n_tiles_max + 1), T256, 16384), T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu, int64_t dt,
+                                  const int32_t* mterm, unsigned* status, int normalise, cudaStream_t s) {
+  k_normalise_rows<<<grid_for(kt, 64, 8192), 64, 0, s>>>(kt, mptr, mval, mclu, dt, mterm, status, normalise);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t* row_ptr, const int32_t* term,
+                               const float* val32, int64_t* lens_then_ptr, int32_t* mterm, double* mval, void* temp,
+                               cudaStream_t s, int phase) {
+  if (phase == 0) {
+    k_gather_lens<<<grid_for(kt, T256, 8192), T256, 0, s>>>(kt, doc_ids, row_ptr, lens_then_ptr);
+    IVF_LAUNCH_CHECK();
+    IVF_CU(exclusive_scan_i64(lens_then_ptr, lens_then_ptr, kt, temp, s));
+  } else {
+    k_gather_copy<<<grid_for(kt * 32, T256, 8192), T256, 0, s>>>(kt, doc_ids, row_ptr, term, val32, lens_then_ptr,
+                                                                 mterm, mval);
+    IVF_LAUNCH_CHECK();
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local_max, const int64_t* row_ptr,
+                                   int32_t* term, const float* val32, void* val_store, int storage, float* nx,
+                                   int32_t n_inst, const int64_t* inst_docs, const int64_t* inst_toff,
+                                   const int32_t* inst_terms, int validate, unsigned* status, cudaStream_t s) {
+  (void)nnz;
+  (void)dt_local_max;
+  const unsigned g = grid_for(n_docs * 32, T256, 16384);
+  switch (storage) {
+    case ST_F16:
+      k_prepare_objects<__half><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, static_cast<__half*>(val_store), nx,
+                                                   n_inst, inst_docs, inst_toff, inst_terms, validate, status);
+      break;
+    case ST_BF16:
+      k_prepare_objects<__nv_bfloat16><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32,
+                                                          static_cast<__nv_bfloat16*>(val_store), nx, n_inst,
+                                                          inst_docs, inst_toff, inst_terms, validate, status);
+      break;
+    default:
+      k_prepare_objects<float><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, nullptr, nx, n_inst, inst_docs,
+                                                  inst_toff, inst_terms, validate, status);
+      break;
+  }
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s) {
+  k_fill_i64<<<grid_for(n, T256, 4096), T256, 0, s>>>(p, n, v);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+}  // namespace ivfk

@@ -1,0 +1,410 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GPU only).
+
+Bar: assignments equal to the FP64 argmax for every object whose FP64 top-2
+gap is >= 1e-6; best similarity within 1e-5 absolute (FP32 storage); the
+objective per object within 1e-5; FP64 master means equal to the oracle's
+update of the same assignment within 1e-12; the visited-entry counter equal
+to Eq. 15's multiplication count exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle.spherical_kmeans as sk
+from paper_2002_09094_gb300 import datagen as dg
+from paper_2002_09094_gb300 import ivf
+from tests.parity_util import assert_report_ok, lockstep
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import __graft_entry__
+
+    __graft_entry__.build()
+
+
+def corpus_for(n_docs, n_terms, mean_len=30.0, zipf=1.1, seed=1, kind="poisson", lo=3, hi=200):
+    return dg.make_corpus(dg.CorpusSpec(n_docs=n_docs, n_terms=n_terms, length_kind=kind, length_mean=mean_len,
+                                        length_lo=lo, length_hi=hi, zipf_s=zipf, seed=seed))
+
+
+# ------------------------------------------------------------ trajectories
+
+
+def test_small_workload_ten_iterations_lockstep():
+    """10,000 Poisson(50) docs, 20,000 terms, Zipf 1.1, K = 100, 10 iterations."""
+    w = dg.SMALL
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    reps = lockstep(c, w.k, ids, w.iterations)
+    for rep in reps:
+        assert_report_ok(rep)
+    # free-running: with no excluded object assigned differently, the GPU
+    # trajectory is the oracle's own trajectory from the same initial state
+    free = sk.iterate(c, sk.initial_means(c, ids), w.iterations, stop_on_convergence=False)
+    diverged = False
+    for rep, it in zip(reps, free):
+        if not diverged:
+            same = np.array_equal(rep["gpu_assign"], it.assign)
+            if not same:
+                excl = it.gap < 1e-6
+                assert np.all((rep["gpu_assign"] == it.assign) | excl)
+                diverged = True
+
+
+@pytest.mark.parametrize("k_tile", [1024, 2048])
+def test_tiled_accumulator_equals_untiled(k_tile):
+    c = corpus_for(4000, 6000, mean_len=40.0)
+    k = 3000
+    ids = dg.init_doc_ids(c.n_docs, k, 5)
+    out = {}
+    for kt in (0, k_tile):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, k_tile=kt if kt else 65536) as m:
+            m.set_means_from_docs(ids)
+            st = m.assign()
+            out[kt] = (m.get_assign(), m.get_best(), m.get_gap(), st["entries_visited"], m.info()["k_tile"])
+    assert out[k_tile][4] == k_tile
+    for q in range(3):
+        assert np.array_equal(out[0][q].view(np.uint32), out[k_tile][q].view(np.uint32))
+    assert out[0][3] == out[k_tile][3]
+    reps = lockstep(c, k, ids, 2, k_tile=k_tile)
+    for rep in reps:
+        assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("k", [1023, 1024, 1025, 4095, 4096, 4097])
+def test_cluster_counts_around_tile_edges(k):
+    c = corpus_for(6000, 5000, mean_len=25.0, seed=k)
+    ids = dg.init_doc_ids(c.n_docs, k, k)
+    for kt in (0, 1024):
+        for rep in lockstep(c, k, ids, 2, k_tile=kt):
+            assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 3e-3), ("bf16", 2.5e-2)])
+def test_mixed_precision_assignments_equal_fp64(storage, tol):
+    c = corpus_for(6000, 8000, mean_len=40.0, seed=3)
+    k = 150
+    ids = dg.init_doc_ids(c.n_docs, k, 9)
+    reps = lockstep(c, k, ids, 3, storage=storage, best_tol=tol)
+    for rep in reps:
+        assert_report_ok(rep)
+    assert sum(r["stats"]["n_rescored"] for r in reps) > 0
+
+
+def test_rescore_off_still_close():
+    c = corpus_for(3000, 4000, seed=4)
+    k = 60
+    ids = dg.init_doc_ids(c.n_docs, k, 4)
+    rep = lockstep(c, k, ids, 1, rescore=False)[0]
+    assert rep["best_ok"]
+    assert rep["stats"]["n_flagged"] == 0 and rep["stats"]["n_rescored"] == 0
+
+
+# ------------------------------------------------------------- batched
+
+
+def test_batched_equals_single_instances():
+    ws = dg.batched_workloads(n_instances=6, n_range=(500, 3000), k_range=(4, 300), d_range=(1000, 6000),
+                              nnz_range=(10.0, 60.0), iterations=4)
+    cs = [dg.make_corpus(w.corpus) for w in ws]
+    ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
+    single = []
+    for w, c, d in zip(ws, cs, ids):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k) as m:
+            m.set_means_from_docs(d)
+            done, conv, _ = m.iterate(4)
+            single.append((m.get_assign(), m.get_means()))
+    inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum([c.nnz for c in cs])])
+    row_ptr = np.concatenate([c.row_ptr[:-1] + o for c, o in zip(cs, offs)] + [[offs[-1]]]).astype(np.int64)
+    term = np.concatenate([c.term for c in cs])
+    val = np.concatenate([c.val for c in cs])
+    with ivf.BatchedIVF(row_ptr, term, val, inst_docs, [c.n_terms for c in cs], [w.k for w in ws]) as m:
+        m.set_means_from_docs(np.concatenate(ids))
+        for _ in range(4):
+            m.assign(stats=False)
+            m.update()
+        a = m.get_assign()
+        ptr, mt, mv = m.get_means()
+    kof = np.concatenate([[0], np.cumsum([w.k for w in ws])])
+    for b, (sa, (sp, st_, sv)) in enumerate(single):
+        assert np.array_equal(a[inst_docs[b]:inst_docs[b + 1]], sa)
+        lo, hi = ptr[kof[b]], ptr[kof[b + 1]]
+        assert np.array_equal(ptr[kof[b]:kof[b + 1] + 1] - lo, sp)
+        assert np.array_equal(mt[lo:hi], st_)
+        assert np.array_equal(mv[lo:hi], sv)
+
+
+def test_batched_lockstep_against_oracle():
+    ws = dg.batched_workloads(n_instances=4, n_range=(800, 2000), k_range=(8, 120), d_range=(2000, 5000),
+                              nnz_range=(15.0, 50.0), iterations=3, seed=77)
+    cs = [dg.make_corpus(w.corpus) for w in ws]
+    ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
+    inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum([c.nnz for c in cs])])
+    row_ptr = np.concatenate([c.row_ptr[:-1] + o for c, o in zip(cs, offs)] + [[offs[-1]]]).astype(np.int64)
+    with ivf.BatchedIVF(row_ptr, np.concatenate([c.term for c in cs]), np.concatenate([c.val for c in cs]),
+                        inst_docs, [c.n_terms for c in cs], [w.k for w in ws]) as m:
+        m.set_means_from_docs(np.concatenate(ids))
+        means = [sk.initial_means(c, d) for c, d in zip(cs, ids)]
+        for r in range(3):
+            st = m.assign()
+            a, bst = m.get_assign(), m.get_best()
+            total_mult = 0
+            for b, c in enumerate(cs):
+                sl = slice(inst_docs[b], inst_docs[b + 1])
+                rep = sk.lockstep_check(c, means[b], a[sl], bst[sl])
+                assert rep["mismatches"] == 0 and rep["best_ok"]
+                total_mult += sk.multiplication_count(c, means[b])
+                means[b] = sk.update(c, a[sl], means[b])[0]
+            assert st["entries_visited"] == total_mult
+            changed = m.get_changed_per_instance()
+            assert changed.sum() == st["n_changed"]
+            m.update()
+
+
+# ------------------------------------------------------------ edge cases
+
+
+def test_k_equals_one_closed_form():
+    c = corpus_for(500, 300, seed=8)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, 1) as m:
+        m.set_means_from_docs([7])
+        m.iterate(3)
+        assert np.all(m.get_assign() == 0)
+        ptr, term, val = m.get_means()
+    total = np.zeros(c.n_terms)
+    np.add.at(total, c.term, c.val.astype(np.float64))
+    nz = np.flatnonzero(total)
+    assert np.array_equal(term, nz)
+    assert np.allclose(val, total[nz] / np.linalg.norm(total), atol=1e-13, rtol=0)
+
+
+def test_each_document_its_own_cluster():
+    c = corpus_for(400, 50000, mean_len=20.0, zipf=0.6, seed=10)  # distinct docs (wide vocabulary)
+    n = c.n_docs
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, n) as m:
+        m.set_means_from_docs(np.arange(n, dtype=np.int32))
+        m.assign()
+        assert np.array_equal(m.get_assign(), np.arange(n))
+        assert np.allclose(m.get_best(), 1.0, atol=1e-6)
+
+
+def test_duplicate_means_tie_lowest_id_and_empty_cluster_policies():
+    c = corpus_for(800, 500, seed=12)
+    ids = dg.init_doc_ids(c.n_docs, 5, 12)
+    dup = np.array([ids[0], ids[1], ids[2], ids[0], ids[3]], dtype=np.int32)  # mean 3 == mean 0
+    for policy in (0, 1):
+        reps = lockstep(c, 5, dup, 3, empty_policy=policy)
+        for rep in reps:
+            assert_report_ok(rep)
+        assert not np.any(reps[0]["gpu_assign"] == 3)  # the higher id of a tie never wins
+        kept = reps[0]["oracle_means_after"].row(3)[0]
+        first = sk.initial_means(c, dup).row(3)[0]
+        assert np.array_equal(kept, first) if policy == 0 else kept.size == 0
+
+
+def test_zero_similarity_objects_and_empty_rows():
+    rows = [([0, 1], [0.6, 0.8]), ([2], [1.0]), ([5, 6], [0.8, 0.6]), ([], []), ([9], [1.0]), ([1, 2], [0.6, 0.8])]
+    c = dg.corpus_from_rows(rows, 10)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, 2) as m:
+        m.set_means_from_docs([0, 1])
+        st = m.assign()
+        a, b = m.get_assign(), m.get_best()
+    assert a.tolist() == [0, 1, 0, 0, 0, 1]
+    assert b[2] == 0.0 and b[3] == 0.0 and b[4] == 0.0
+    assert st["n_zero_sim"] == 3
+
+
+@pytest.mark.parametrize("n", [1, 2, 33, 1000])
+def test_ragged_tiny_collections(n):
+    c = corpus_for(n, 64, mean_len=5.0, seed=n, lo=1, hi=20)
+    k = max(1, min(n, 7))
+    ids = dg.init_doc_ids(n, k, n)
+    for rep in lockstep(c, k, ids, 3):
+        assert_report_ok(rep)
+
+
+def test_long_posting_lists():
+    """A head term in every document: its list is as long as K (here 20,000)."""
+    c = corpus_for(30000, 3000, mean_len=30.0, zipf=1.3, seed=14)
+    k = 20000
+    ids = dg.init_doc_ids(c.n_docs, k, 14)
+    rows = np.random.default_rng(0).choice(c.n_docs, 500, replace=False)
+    for rep in lockstep(c, k, ids, 2, rows=rows):
+        assert_report_ok(rep, check_objective=False)
+
+
+# ------------------------------------------------------ state and layout
+
+
+def test_checkpoint_resume_bit_exact():
+    c = corpus_for(5000, 6000, seed=15)
+    k = 80
+    ids = dg.init_doc_ids(c.n_docs, k, 15)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        m.iterate(10)
+        a10, means10 = m.get_assign(), m.get_means()
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        m.iterate(5)
+        a5, (p5, t5, v5) = m.get_assign(), m.get_means()
+        it5 = m.info()["iteration"]
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.restore_means(p5, t5, v5, it5)
+        m.set_assign(a5)
+        m.iterate(5)
+        assert m.info()["iteration"] == 10
+        b10, bm = m.get_assign(), m.get_means()
+    assert np.array_equal(a10, b10)
+    for x, y in zip(means10, bm):
+        assert np.array_equal(x, y)
+
+
+def test_graph_iterations_equal_eager():
+    c = corpus_for(4000, 5000, seed=16)
+    k = 64
+    ids = dg.init_doc_ids(c.n_docs, k, 16)
+    res = []
+    for g in (True, False):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, use_graph=g) as m:
+            m.set_means_from_docs(ids)
+            done, conv, st = m.iterate(8)
+            res.append((done, conv, m.get_assign(), m.get_best(), m.get_means()))
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        for _ in range(res[0][0]):
+            m.assign(stats=False)
+            m.update()
+        res.append((res[0][0], res[0][1], m.get_assign(), m.get_best(), m.get_means()))
+    for other in res[1:]:
+        assert other[0] == res[0][0] and other[1] == res[0][1]
+        assert np.array_equal(other[2], res[0][2])
+        assert np.array_equal(other[3].view(np.uint32), res[0][3].view(np.uint32))
+        for x, y in zip(other[4], res[0][4]):
+            assert np.array_equal(x, y)
+
+
+def test_runs_are_bit_reproducible():
+    c = corpus_for(6000, 7000, seed=17)
+    k = 120
+    ids = dg.init_doc_ids(c.n_docs, k, 17)
+    outs = []
+    for _ in range(2):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(4)
+            m.assign(stats=False)
+            outs.append((m.get_best().view(np.uint32), m.get_gap().view(np.uint32)))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_inverted_file_layout_and_members():
+    c = corpus_for(3000, 4000, seed=18)
+    k = 50
+    ids = dg.init_doc_ids(c.n_docs, k, 18)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        m.assign(stats=False)
+        a = m.get_assign()
+        m.update()
+        tp, cid, w = m.get_inverted_file()
+        ptr, term, val = m.get_means()
+        cl, mem = m.get_members()
+    # every list ascends strictly in cluster id; E = sum_p (nc)_p = sum_j (ntm)_j
+    assert tp[0] == 0 and tp[-1] == ptr[-1] == cid.size
+    owner = np.repeat(np.arange(c.n_terms), np.diff(tp))
+    same = owner[1:] == owner[:-1]
+    assert np.all(np.diff(cid.astype(np.int64))[same] > 0)
+    # the inverted file is the transpose of the cluster-major means, values cast once to FP32
+    rows = np.repeat(np.arange(k), np.diff(ptr))
+    order = np.lexsort((rows, term))
+    assert np.array_equal(cid, rows[order])
+    assert np.array_equal(w, val[order].astype(np.float32))
+    # C_j: objects grouped by cluster in ascending id
+    assert np.array_equal(mem, np.argsort(a, kind="stable"))
+    assert np.array_equal(cl, np.concatenate([[0], np.cumsum(np.bincount(a, minlength=k))]))
+
+
+def test_set_means_rows_normalised():
+    c = corpus_for(2000, 3000, seed=19)
+    k = 30
+    ids = dg.init_doc_ids(c.n_docs, k, 19)
+    # means given as raw rows scaled by 3: the library divides by the norm
+    m0 = sk.initial_means(c, ids)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means(m0.ptr, m0.term.astype(np.int32), (3.0 * m0.val).astype(np.float32))
+        m.assign()
+        a = m.get_assign()
+    ref = sk.means_from_rows(m0.ptr, m0.term, (3.0 * m0.val).astype(np.float32).astype(np.float64), c.n_terms)
+    rep = sk.lockstep_check(c, ref, a)
+    assert rep["mismatches"] == 0
+
+
+# -------------------------------------------------------------- errors
+
+
+def test_errors_are_statuses_not_crashes():
+    c = corpus_for(200, 100, seed=20)
+    with pytest.raises(ivf.IvfError) as e:
+        ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, c.n_docs + 1)
+    assert e.value.status == ivf.IVF_E_INVALID
+    bad = c.row_ptr.copy()
+    bad[5] = bad[6] + 1
+    with pytest.raises(ivf.IvfError):
+        ivf.IVF(bad, c.term, c.val, c.n_terms, 4)
+    t2 = c.term.copy()
+    t2[c.row_ptr[3]], t2[c.row_ptr[3] + 1] = t2[c.row_ptr[3] + 1], t2[c.row_ptr[3]]  # unsorted row
+    with pytest.raises(ivf.IvfError) as e:
+        ivf.IVF(c.row_ptr, t2, c.val, c.n_terms, 4, validate=True)
+    assert e.value.status == ivf.IVF_E_INVALID
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, 4) as m:
+        with pytest.raises(ivf.IvfError) as e:
+            m.assign()
+        assert e.value.status == ivf.IVF_E_STATE
+        with pytest.raises(ivf.IvfError) as e:
+            m.update()
+        assert e.value.status == ivf.IVF_E_STATE
+        with pytest.raises(ivf.IvfError) as e:
+            m.set_means_from_docs([1, 1, 2, 3])
+        assert e.value.status == ivf.IVF_E_INVALID
+        with pytest.raises(ivf.IvfError):
+            m.set_means_from_docs([1, 2, 3, 999])
+        with pytest.raises(ivf.IvfError) as e:
+            m.set_means(np.array([0, 1, 1, 2, 3]), np.array([0, 1, 2], np.int32), np.array([1, 1, 1], np.float32))
+        assert e.value.status == ivf.IVF_E_INVALID  # an empty (zero-norm) mean row
+        # still usable after the errors
+        m.set_means_from_docs([1, 2, 3, 4])
+        m.assign()
+        m.update()
+
+
+# ----------------------------------------------- full-size sampled parity
+
+
+def test_scale_workload_sampled_lockstep():
+    """1,000,000 docs x 500,000 terms, K = 10,000, in the benchmark's launch
+    shape: two iterations, 2,000 sampled objects plus every near-tie the GPU
+    flagged, means checked in full, Eq. 15 exact at full size."""
+    w = dg.SCALE
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    rows = np.random.default_rng(123).choice(c.n_docs, 2000, replace=False)
+    reps = lockstep(c, w.k, ids, 2, rows=rows)
+    for rep in reps:
+        assert_report_ok(rep, check_objective=False)
+
+
+def test_large_k_tiled_sampled_lockstep():
+    """K = 80,000 (> 65,536: tiled accumulator and 16-bit tile-local ids) on
+    200,000 docs x 2,000,000 terms, lognormal(80) lengths, Zipf 1.0."""
+    w = dg.LARGE.scaled(n_docs=200_000, name="large-k-200k-docs")
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    rows = np.random.default_rng(7).choice(c.n_docs, 1000, replace=False)
+    reps = lockstep(c, w.k, ids, 2, rows=rows)
+    for rep in reps:
+        assert_report_ok(rep, check_objective=False)
