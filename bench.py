@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="ivf-scale-n1m-d500k-k10k")
     p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
+    p.add_argument("--n-docs", type=int, default=0, help="use only this many documents of the workload "
+                   "(same generator; for small profiling cases)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -179,6 +181,15 @@ def oracle_iteration_sample(corpus, means, assign_for_update, rng, budget_s: flo
     return t_assign + t_update, desc
 
 
+def workload(args):
+    from paper_2002_09094_gb300 import datagen as dg
+
+    w = dg.WORKLOADS[args.workload]
+    if args.n_docs:
+        w = w.scaled(n_docs=args.n_docs, name=f"{w.name}-first{args.n_docs}")
+    return w
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -190,7 +201,7 @@ def run_reference(args, rank, world):
     import oracle.spherical_kmeans as sk
     from paper_2002_09094_gb300 import datagen as dg
 
-    w = dg.WORKLOADS[args.workload]
+    w = workload(args)
     c = dg.make_corpus(w.corpus)
     ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
     means = sk.initial_means(c, ids)
@@ -234,7 +245,7 @@ def run_ours(args, rank, world, local):
         if dist is not None:
             dist.barrier()
 
-    w = dg.WORKLOADS[args.workload]
+    w = workload(args)
     t0 = time.time()
     c = dg.make_corpus(w.corpus)
     gen_s = time.time() - t0

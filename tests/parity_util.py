@@ -25,13 +25,22 @@ def means_report(gpu_means, oracle_means) -> dict:
     return {"structure_equal": bool(same), "max_diff": diff}
 
 
-def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, **kw):
-    """Run `iters` GPU iterations (assign + update) with oracle checks; returns reports."""
+def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, means_rows=None, **kw):
+    """Run `iters` GPU iterations (assign + update) with oracle checks; returns reports.
+
+    Initial means: documents doc_ids, or explicit cluster-major rows
+    means_rows = (ptr, term, val32) when given.
+    """
     m = ivf.IVF(corpus.row_ptr, corpus.term, corpus.val, corpus.n_terms, k, **kw)
     empty_policy = kw.get("empty_policy", 0)
     try:
-        m.set_means_from_docs(doc_ids)
-        means = sk.initial_means(corpus, doc_ids)
+        if means_rows is None:
+            m.set_means_from_docs(doc_ids)
+            means = sk.initial_means(corpus, doc_ids)
+        else:
+            mp, mt, mv = means_rows
+            m.set_means(mp, np.asarray(mt, np.int32), np.asarray(mv, np.float32))
+            means = sk.means_from_rows(mp, mt, np.asarray(mv, np.float32).astype(np.float64), corpus.n_terms)
         prev = None
         reports = []
         for r in range(1, iters + 1):
@@ -44,6 +53,7 @@ def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, **kw):
             rep = sk.lockstep_check(corpus, means, a, b, rows=sample, gap_exclusion=GAP_EXCLUSION,
                                     best_tol=best_tol)
             rep["r"] = r
+            rep["best_tol"] = best_tol
             rep["stats"] = st
             rep["mult_count"] = sk.multiplication_count(corpus, means)
             rep["n_changed_expected"] = corpus.n_docs if prev is None else int(np.count_nonzero(a != prev))
@@ -72,7 +82,7 @@ def assert_report_ok(rep, check_best=True, check_means=True, check_objective=Tru
     assert st["n_changed"] == rep["n_changed_expected"]
     if check_objective and rep["objective_expected"] is not None:
         n = rep["checked"]
-        assert abs(st["objective"] - rep["objective_expected"]) / n <= BEST_TOL
+        assert abs(st["objective"] - rep["objective_expected"]) / n <= rep["best_tol"]
     if check_means:
         assert rep["means"]["structure_equal"], rep["r"]
         assert rep["means"]["max_diff"] <= MEAN_TOL, rep["means"]
