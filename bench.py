@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     p.add_argument("--n-docs", type=int, default=0, help="use only this many documents of the workload "
                    "(same generator; for small profiling cases)")
+    p.add_argument("--kernel", choices=["auto", "dense_head", "sparse"], default="auto",
+                   help="assignment kernel family (auto = the autotuner picks)")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -109,9 +111,12 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t_begin: float, t_end: float):
+        """Stop sampling; summarise the samples taken between t_begin and t_end
+        (host wall clock).  The sampler starts before the warm-up, so its own
+        start-up never overlaps the timed region."""
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -121,7 +126,8 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for ts, ln in self.lines if t_begin <= ts <= t_end + 0.25]
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -190,6 +196,15 @@ def workload(args):
     return w
 
 
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """Largest value over all ranks (the slowest replica sets the job time)."""
+    import torch
+
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
@@ -253,22 +268,24 @@ def run_ours(args, rank, world, local):
     stream = torch.cuda.Stream()
     bv = 4 if args.storage == "f32" else 2
     with torch.cuda.stream(stream):
-        m = ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage, stream=stream.cuda_stream)
+        m = ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage, stream=stream.cuda_stream,
+                    kernel=args.kernel)
         m.set_means_from_docs(ids)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
         for _ in range(args.warmup):
             m.assign(stats=False)
             m.update()
         torch.cuda.synchronize()
         barrier()
         # ---------------------------------------------------------- timed region
-        clocks = ClockSampler(torch.cuda.current_device())
-        clocks.start()
         m.timing_reset(True)
         launches0 = ivf.launch_count()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         barrier()
+        t_begin = time.time()
         ev0.record(stream)
         for _ in range(args.steps):
             m.assign(stats=False)
@@ -276,16 +293,15 @@ def run_ours(args, rank, world, local):
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
+        t_end = time.time()
         total_ms = ev0.elapsed_time(ev1)
         launches = ivf.launch_count() - launches0
-        clk = clocks.stop()
+        clk = clocks.stop(t_begin, t_end)
         timing = m.get_timing()
         m.timing_reset(False)
         info = m.info()
         if dist is not None:
-            t = torch.tensor([total_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, dist, "cuda")
         # ------------------------------------------------------ end to end
         # each step: host->device copy of the objects from pinned memory, one
         # iteration, device->host read of the assignment
@@ -333,6 +349,8 @@ def run_ours(args, rank, world, local):
                       "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (CSR %.2f GB); no flush" % (c.nnz * 8 / 1e9),
                       "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"],
+                      "kernel": ("dense_head r=%d theta=%.2f rows=%d" % (info["dense_head_r"], info["dense_head_theta"],
+                                 info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
                       "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},
            "phases_ms_per_step": {"assign_kernel": round(kern_ms, 4),
                                   "assign_step": round(timing["assign_step_ms"] / n_steps, 4),

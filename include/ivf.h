@@ -63,6 +63,11 @@ typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
 /* ivf_config.flags */
 #define IVF_FLAG_VALIDATE 1u  /* check CSR rows (sorted, unique, in range, finite) at create/load */
 #define IVF_FLAG_NO_GRAPH 2u  /* ivf_iterate launches kernels directly instead of a CUDA graph */
+#define IVF_FLAG_DENSE_HEAD 4u  /* autotune only among dense-head kernels: posting lists that cover
+                                   at least a fraction theta of the K clusters are also stored as
+                                   dense rows (the paper's full inverted file, IFN, Section 4,
+                                   for those terms only) and accumulated in registers */
+#define IVF_FLAG_SPARSE_ONLY 8u /* autotune only among kernels that read the sparse lists alone */
 
 typedef struct {
   int64_t n_docs;      /* N >= 1 */
@@ -105,6 +110,9 @@ typedef struct {
   int32_t iteration;       /* completed update steps */
   int32_t storage;
   int64_t device_bytes;    /* device memory held by the context */
+  int32_t dense_head_r;    /* 0: sparse kernel; else dense-head kernel with a 32*r-cluster tile */
+  float dense_head_theta;  /* lists covering >= theta * K clusters are stored densely */
+  int64_t dense_head_rows; /* dense rows in the inverted file last built */
 } ivf_info;
 
 /* Create a context for one clustering problem and copy the objects in.

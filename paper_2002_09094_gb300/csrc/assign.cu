@@ -27,6 +27,7 @@ namespace ivfk {
 namespace {
 
 constexpr int kMaxThreads = 1024;
+constexpr int kMaxThreadsHead = 32 * HEAD_MAX_WARPS;  // register accumulators need more than 64 registers
 
 __device__ __forceinline__ void top2_push(float& b, int& id, float& s, float x, int xid) {
   if (x > b || (x == b && xid < id)) {
@@ -82,7 +83,9 @@ __device__ __forceinline__ float err_bound(int m, float nx, int storage) {
   const float u32 = 5.9604645e-08f;  // 2^-24
   const float S = nx * 1.000001f;
   const float fm = (float)m;
-  const float g = fm * u32 / (1.f - fm * u32);
+  // m + 1 roundings at most per rho_c: up to m FMAs in the head and tail
+  // chains together, plus the one addition that joins them
+  const float g = (fm + 1.f) * u32 / (1.f - (fm + 1.f) * u32);
   float e;
   if (storage == ST_F32) {
     e = S * (u32 + g * (1.f + u32));
@@ -118,8 +121,14 @@ __device__ __forceinline__ void prune_candidates(int* cand_id, float* cand_val, 
   __syncwarp();
 }
 
-template <typename WT>
-__global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
+// R > 0: hybrid kernel.  Posting lists stored as dense head rows are
+// accumulated in registers -- lane l owns clusters l, l+32, ..., l+32(R-1) of
+// the tile (tile = 32R clusters) -- so they need neither cluster ids nor
+// shared-memory read-modify-writes; the remaining (sparse) lists scatter into
+// the shared-memory tile as in the R = 0 kernel.  Per cluster the head and
+// the tail contributions are each summed in ascending term order, then added.
+template <typename WT, typename IdT, int R>
+__global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assign(const AssignArgs a) {
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* rho = smem + (size_t)warp * (a.tile_cap + 2 * CAND_MAX);
@@ -127,7 +136,11 @@ __global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
   float* cand_val = rho + a.tile_cap + CAND_MAX;
   const WT* __restrict__ val = static_cast<const WT*>(a.val);
   const WT* __restrict__ w = static_cast<const WT*>(a.w);
-  const uint16_t* __restrict__ cid = a.cid;
+  const IdT* __restrict__ cid = static_cast<const IdT*>(a.cid);
+  const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
+  const int32_t* __restrict__ head_slot = a.head_slot;
+  constexpr int RR = R > 0 ? R : 1;
+  float acc[RR];
   const int cmask = a.tiled ? (a.k_tile - 1) : 0xFFFF;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long my_entries = 0;
@@ -156,16 +169,20 @@ __global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
       // rho <- 0 over the tile
       float4* r4 = reinterpret_cast<float4*>(rho);
       for (int q = lane; q < ((cnt + 3) >> 2); q += 32) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < RR; ++r) acc[r] = 0.f;
       __syncwarp();
       // for s in S_i (32 at a time): for (c, u) in xi_s: rho_c += v * u
       for (int64_t h0 = r0; h0 < r1; h0 += 32) {
         const int64_t h = h0 + lane;
         int64_t beg = 0;
         int len = 0;
+        int slot = -1;
         float v = 0.f;
         if (h < r1) {
           const int t = __ldg(a.term + h);
           v = to_f32(val[h]);
+          if (R > 0 && head_slot != nullptr) slot = __ldg(head_slot + t);
           const int64_t tb = __ldg(a.term_ptr + t);
           if (a.tiled) {
             const int32_t* to = a.toff + (int64_t)t * (a.n_tiles_max + 1) + tt;
@@ -183,7 +200,16 @@ __global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
           const int64_t bj = __shfl_sync(IVF_FULL_MASK, beg, j);
           const int lj = __shfl_sync(IVF_FULL_MASK, len, j);
           const float vj = __shfl_sync(IVF_FULL_MASK, v, j);
-          const uint16_t* __restrict__ cp = cid + bj;
+          if (R > 0) {
+            const int sj = __shfl_sync(IVF_FULL_MASK, slot, j);
+            if (sj >= 0) {  // dense head row: acc[r] += v * w[lo + lane + 32 r]
+              const WT* __restrict__ row = wd + (int64_t)sj * a.kpad + lo + lane;
+#pragma unroll
+              for (int r = 0; r < RR; ++r) acc[r] = fmaf(vj, to_f32(__ldg(row + 32 * r)), acc[r]);
+              continue;
+            }
+          }
+          const IdT* __restrict__ cp = cid + bj;
           const WT* __restrict__ wp = w + bj;
           int q = lane;
           for (; q + 96 < lj; q += 128) {
@@ -210,7 +236,19 @@ __global__ void __launch_bounds__(kMaxThreads) k_assign(const AssignArgs a) {
       // argmax over the tile: lowest id among the maxima, plus the runner-up
       float tb = -INFINITY, ts = -INFINITY;
       int ti = 0x7fffffff;
-      for (int q = lane; q < cnt; q += 32) top2_push(tb, ti, ts, rho[q], lo + q);
+      if (R > 0) {  // rho_c = head part (registers) + tail part (shared memory)
+#pragma unroll
+        for (int r = 0; r < RR; ++r) {
+          const int q = lane + 32 * r;
+          if (q < cnt) {
+            const float x = acc[r] + rho[q];
+            rho[q] = x;
+            top2_push(tb, ti, ts, x, lo + q);
+          }
+        }
+      } else {
+        for (int q = lane; q < cnt; q += 32) top2_push(tb, ti, ts, rho[q], lo + q);
+      }
       warp_top2(tb, ti, ts);
       top2_merge(best, bid, second, tb, ti, ts);
       if (e2 >= 0.f) {
@@ -412,18 +450,40 @@ __global__ void k_reduce_final(const ReduceArgs a, int nblocks) {
 }
 
 template <typename WT>
-const void* assign_fn() {
-  return reinterpret_cast<const void*>(&k_assign<WT>);
+const void* assign_fn_r(int head_r) {
+  switch (head_r) {
+    case HEAD_R_SMALL:
+      return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_SMALL>);
+    case HEAD_R_LARGE:
+      return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE>);
+    default:
+      return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, 0>);
+  }
 }
 
-const void* assign_fn_for(int storage) {
+const void* assign_fn_for(int storage, int head_r) {
   switch (storage) {
     case ST_F16:
-      return assign_fn<__half>();
+      return assign_fn_r<__half>(head_r);
     case ST_BF16:
-      return assign_fn<__nv_bfloat16>();
+      return assign_fn_r<__nv_bfloat16>(head_r);
     default:
-      return assign_fn<float>();
+      return assign_fn_r<float>(head_r);
+  }
+}
+
+template <typename WT>
+void launch_typed(const AssignArgs& a, int warps, int blocks, size_t smem, cudaStream_t s, int head_r) {
+  switch (head_r) {
+    case HEAD_R_SMALL:
+      k_assign<WT, uint16_t, HEAD_R_SMALL><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+    case HEAD_R_LARGE:
+      k_assign<WT, uint16_t, HEAD_R_LARGE><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+    default:
+      k_assign<WT, uint16_t, 0><<<blocks, warps * 32, smem, s>>>(a);
+      break;
   }
 }
 
@@ -433,31 +493,32 @@ size_t assign_smem_bytes(int tile_cap, int warps) {
   return (size_t)warps * ((size_t)tile_cap + 2 * CAND_MAX) * sizeof(float);
 }
 
-cudaError_t assign_prepare(int storage, int tile_cap, int warps) {
+cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r) {
   const size_t bytes = assign_smem_bytes(tile_cap, warps);
-  return cudaFuncSetAttribute(assign_fn_for(storage), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaFuncSetAttribute(assign_fn_for(storage, head_r), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
 }
 
-int assign_max_blocks_per_sm(int storage, int tile_cap, int warps) {
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r) {
   int nb = 0;
-  if (assign_prepare(storage, tile_cap, warps) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage), warps * 32,
+  if (assign_prepare(storage, tile_cap, warps, head_r) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage, head_r), warps * 32,
                                                     assign_smem_bytes(tile_cap, warps)) != cudaSuccess)
     return 0;
   return nb;
 }
 
-cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s) {
+cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r) {
   const size_t smem = assign_smem_bytes(a.tile_cap, warps);
   switch (a.storage) {
     case ST_F16:
-      k_assign<__half><<<blocks, warps * 32, smem, s>>>(a);
+      launch_typed<__half>(a, warps, blocks, smem, s, head_r);
       break;
     case ST_BF16:
-      k_assign<__nv_bfloat16><<<blocks, warps * 32, smem, s>>>(a);
+      launch_typed<__nv_bfloat16>(a, warps, blocks, smem, s, head_r);
       break;
     default:
-      k_assign<float><<<blocks, warps * 32, smem, s>>>(a);
+      launch_typed<float>(a, warps, blocks, smem, s, head_r);
       break;
   }
   IVF_LAUNCH_CHECK();

@@ -4,6 +4,7 @@
 // and launches.
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -38,6 +39,7 @@ struct DevCounters {
   long long ivf_e;            // entries of the inverted file last built
   unsigned long long acc_entries;   // timing window sums
   unsigned long long acc_rescored;
+  long long heads;                  // dense head rows of the inverted file last built
 };
 
 struct Shape {
@@ -46,7 +48,12 @@ struct Shape {
   int tiled = 0;
   int warps = 0;
   int blocks = 0;
+  int head_r = 0;     // registers per lane of the dense-head accumulator (0 = no dense head)
+  float head_theta = 0.f;  // a list covering at least this fraction of K is stored densely
 };
+
+// Dense head rows may use at most this much device memory.
+constexpr int64_t kHeadBudgetBytes = int64_t(2) << 30;
 
 std::mutex g_tune_mu;
 std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, Shape> g_tune_cache;
@@ -98,6 +105,12 @@ struct ivf_ctx {
   int32_t* toff = nullptr;
   int64_t toff_len = 0;
   int64_t* d_e = nullptr;  // points into dc
+  // dense head rows
+  int32_t* head_slot = nullptr;
+  uint32_t* hflags = nullptr;
+  void* wd = nullptr;
+  int64_t kpad = 0;
+  int64_t head_max = 0;
   // assignment
   int32_t* assign[2] = {nullptr, nullptr};
   int alatest = -1;  // buffer holding the latest assignment, -1 = none
@@ -137,6 +150,7 @@ struct ivf_ctx {
   // launch shape
   Shape shape;
   bool tuned = false;
+  bool tuned_on_updated_means = false;  // the choice was made on means from an update step
   // state
   bool means_set = false;
   int32_t iteration = 0;
@@ -469,7 +483,39 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
   a.v32b = c->v32b;
   a.temp = c->temp;
   a.status = &c->dc->status;
+  if (c->shape.head_r > 0 && c->head_slot) {
+    a.head_slot = c->head_slot;
+    a.wd = c->wd;
+    a.kpad = c->kpad;
+    a.head_max = c->head_max;
+    a.head_min_nc = std::max<int64_t>(1, (int64_t)std::ceil((double)c->shape.head_theta * c->kmax));
+    a.hflags = c->hflags;
+    a.d_heads = reinterpret_cast<int64_t*>(&c->dc->heads);
+  }
   return a;
+}
+
+// Buffers of the dense head rows for tiles of 32 * head_r clusters.
+ivf_status alloc_head(ivf_ctx* c, int head_r) {
+  const int64_t tile = 32 * (int64_t)head_r;
+  const int64_t kpad = ceil_div(c->kmax, tile) * tile;
+  if (c->head_slot && c->kpad == kpad) return IVF_OK;
+  dfree(c, c->head_slot);
+  dfree(c, c->hflags);
+  dfree(c, c->wd);
+  c->head_slot = nullptr;
+  c->hflags = nullptr;
+  c->wd = nullptr;
+  const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
+  c->head_max = std::max<int64_t>(1, std::min<int64_t>(c->Dt, kHeadBudgetBytes / (kpad * vb)));
+  c->kpad = kpad;
+  ST(dalloc(c, &c->head_slot, c->Dt));
+  ST(dalloc(c, &c->hflags, c->Dt + 1));
+  char* p = nullptr;
+  ST(dalloc(c, &p, c->head_max * kpad * vb));
+  c->wd = p;
+  drop_graphs(c);
+  return IVF_OK;
 }
 
 // Stream-ordered: rebuild the inverted file from means buffer mb.
@@ -509,29 +555,42 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
   a.flag_obj = c->flag_obj;
   a.flag_cnt = c->flag_cnt;
   a.flag_cand = c->flag_cand;
+  if (sh.head_r > 0) {
+    a.head_slot = c->head_slot;
+    a.wd = c->wd;
+    a.kpad = c->kpad;
+  }
   return a;
 }
 
-bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out) {
+// head_r > 0 selects the dense-head kernel, whose tile is 32 * head_r clusters.
+bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f) {
   Shape sh;
+  if (head_r > 0) {
+    if (c->n_inst != 1) return false;
+    k_tile = 32 * head_r;
+  }
   if (k_tile <= 0 || k_tile >= c->kmax) {
     if (c->kmax > 65536) return false;
     sh.tiled = 0;
     sh.k_tile = c->kmax;
     sh.tile_cap = (c->kmax + 3) & ~3;
   } else {
-    if (!is_pow2(k_tile) || k_tile < 512 || k_tile > 65536) return false;
+    if (!is_pow2(k_tile) || k_tile < (head_r > 0 ? 256 : 512) || k_tile > 65536) return false;
     sh.tiled = 1;
     sh.k_tile = k_tile;
     sh.tile_cap = k_tile;
   }
+  sh.head_r = head_r;
+  sh.head_theta = theta;
   const size_t per_warp = ((size_t)sh.tile_cap + 2 * CAND_MAX) * sizeof(float);
-  int wmax = (int)std::min<size_t>(kSmemBudget / per_warp, 16);
+  int wmax = (int)std::min<size_t>(kSmemBudget / per_warp, head_r > 0 ? HEAD_MAX_WARPS : 16);
   if (wmax < 1) return false;
+  if (head_r > 0 && warps_req > HEAD_MAX_WARPS) return false;
   int warps = warps_req > 0 ? std::min(warps_req, wmax) : std::min(wmax, 8);
   if (warps_req > 0 && (size_t)warps_req * per_warp > kSmemBudget) return false;
   sh.warps = warps;
-  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps);
+  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps, head_r);
   if (bps < 1) return false;
   sh.blocks = bps * c->num_sms;
   *out = sh;
@@ -540,14 +599,20 @@ bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out) {
 
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   c->shape = sh;
-  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps));
-  if (sh.tiled) {
-    IvfBuildArgs a = ivf_args(c, c->mcur);
-    CK(c, launch_build_toff(a, c->stream));
-  }
+  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r));
+  if (sh.head_r > 0) ST(alloc_head(c, sh.head_r));
+  IvfBuildArgs a = ivf_args(c, c->mcur);
+  if (sh.tiled) CK(c, launch_build_toff(a, c->stream));
+  if (sh.head_r > 0) CK(c, launch_build_head(a, c->stream));
   drop_graphs(c);
   return IVF_OK;
 }
+
+// The first choice is made on the initial means (single documents: short
+// posting lists); the lists of updated means are far denser, which favours
+// other kernels, so the choice is made once more on the first assignment
+// after an update step.
+bool needs_tuning(const ivf_ctx* c) { return !c->tuned || (!c->tuned_on_updated_means && c->iteration > 0); }
 
 ivf_status autotune(ivf_ctx* c) {
   std::vector<Shape> cands;
@@ -557,24 +622,37 @@ ivf_status autotune(ivf_ctx* c) {
       return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
     cands.push_back(sh);
   } else {
-    if (shape_for(c, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
-    for (int t : kTileChoices)
-      if (t < c->kmax && shape_for(c, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+    const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0;
+    const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0;
+    if (!head_only) {
+      if (shape_for(c, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+      for (int t : kTileChoices)
+        if (t < c->kmax && shape_for(c, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+    }
+    // dense-head kernels (the IFN form for lists covering >= theta K clusters)
+    const int hr = c->kmax <= 32 * HEAD_R_SMALL ? HEAD_R_SMALL : HEAD_R_LARGE;
+    if (!no_head)
+      for (float theta : {0.5f, 0.25f})
+        if (shape_for(c, 0, c->cfg.warps_per_block, &sh, hr, theta)) cands.push_back(sh);
   }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
-  auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12, c->cfg.storage, c->n_inst);
+  auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
+                             (c->cfg.storage * 16 + (int)c->cfg.flags) * 2 + (c->iteration > 0 ? 1 : 0),
+                             c->n_inst);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end() && c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
       ST(set_shape(c, it->second));
       c->tuned = true;
+      c->tuned_on_updated_means = c->iteration > 0;
       return IVF_OK;
     }
   }
   if (cands.size() == 1) {
     ST(set_shape(c, cands[0]));
     c->tuned = true;
+    c->tuned_on_updated_means = c->iteration > 0;
     return IVF_OK;
   }
   // Time one assignment per candidate (no re-score) on the real data.
@@ -588,7 +666,7 @@ ivf_status autotune(ivf_ctx* c) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(c, cudaMemsetAsync(c->dc, 0, sizeof(unsigned long long) * 2, c->stream));
       CK(c, cudaEventRecord(c->ev[0], c->stream));
-      CK(c, launch_assign(a, cand.warps, cand.blocks, c->stream));
+      CK(c, launch_assign(a, cand.warps, cand.blocks, c->stream, cand.head_r));
       CK(c, cudaEventRecord(c->ev[1], c->stream));
       CK(c, cudaEventSynchronize(c->ev[1]));
       float ms = 0.f;
@@ -602,6 +680,7 @@ ivf_status autotune(ivf_ctx* c) {
   }
   ST(set_shape(c, best_sh));
   c->tuned = true;
+  c->tuned_on_updated_means = c->iteration > 0;
   if (c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best_sh;
@@ -630,7 +709,7 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
   AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
   size_t e0 = 0, e1 = 0, e2 = 0;
   if (timed) CK(c, timing_event(c, &e0));
-  CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s));
+  CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
   if (timed) CK(c, timing_event(c, &e1));
   if (c->cfg.rescore) {
     RescoreArgs r{};
@@ -957,7 +1036,7 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
 ivf_status ivf_assign(ivf_ctx* c, int32_t* assign_out, float* best_out, float* gap_out, ivf_iter_stats* stats_out) {
   if (!c) return IVF_E_INVALID;
   if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
-  if (!c->tuned) ST(autotune(c));
+  if (needs_tuning(c)) ST(autotune(c));
   const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
   const int prev = c->alatest;
   CK(c, cudaEventRecord(c->ev[0], c->stream));
@@ -998,10 +1077,11 @@ ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_
   if (!c) return IVF_E_INVALID;
   if (max_iter < 0) return fail(c, IVF_E_INVALID, "max_iter < 0");
   if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
-  if (!c->tuned) ST(autotune(c));
+  if (needs_tuning(c)) ST(autotune(c));
   int32_t done = 0, conv = 0;
   const bool use_graph = !(c->cfg.flags & IVF_FLAG_NO_GRAPH);
   for (int32_t r = 1; r <= max_iter; ++r) {
+    if (needs_tuning(c)) ST(autotune(c));
     const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
     const int prev = c->alatest;
     if (use_graph && prev >= 0) {
@@ -1093,6 +1173,13 @@ ivf_status ivf_get_info(ivf_ctx* c, ivf_info* out) {
   out->iteration = c->iteration;
   out->storage = c->cfg.storage;
   out->device_bytes = c->bytes;
+  out->dense_head_r = c->shape.head_r;
+  out->dense_head_theta = c->shape.head_theta;
+  long long heads = 0;
+  if (c->shape.head_r > 0) {
+    CK(c, cudaMemcpy(&heads, &c->dc->heads, sizeof(long long), cudaMemcpyDeviceToHost));
+  }
+  out->dense_head_rows = heads;
   return IVF_OK;
 }
 

@@ -29,7 +29,7 @@ struct AssignArgs {
   const int64_t* inst_docs;  // [n_inst+1]
   const int32_t* inst_clu;   // [n_inst+1]
   const int64_t* term_ptr;   // [D+1]
-  const uint16_t* cid;       // [E] local cluster id & 0xFFFF
+  const void* cid;           // [E] local cluster id & 0xFFFF (uint16), or int32 ids
   const void* w;             // [E] storage type
   const int32_t* toff;       // [D * (n_tiles_max+1)] per (term, tile) offset inside the list, or null
   int32_t n_tiles_max;
@@ -47,12 +47,23 @@ struct AssignArgs {
   int32_t* flag_obj;            // [N]
   int32_t* flag_cnt;            // [N] candidates, -1 = overflow (all clusters)
   int32_t* flag_cand;           // [N * CAND_MAX]
+  // Dense head rows (the IFN form for the densest posting lists): term t with
+  // head_slot[t] >= 0 is read from wd[head_slot[t] * kpad + cluster] instead
+  // of its sparse list.  Used by the register-accumulator kernels (head_r > 0).
+  const int32_t* head_slot;     // [D] or null
+  const void* wd;               // [T * kpad] storage type
+  int64_t kpad;                 // row length, a multiple of the tile (32 * head_r)
 };
 
+// Registers per lane of the head accumulator; the tile is 32 * R clusters.
+constexpr int HEAD_R_SMALL = 8;
+constexpr int HEAD_R_LARGE = 32;
+constexpr int HEAD_MAX_WARPS = 8;  // warps per block of the dense-head kernels
+
 size_t assign_smem_bytes(int tile_cap, int warps);
-cudaError_t assign_prepare(int storage, int tile_cap, int warps);
-cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s);
-int assign_max_blocks_per_sm(int storage, int tile_cap, int warps);
+cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r = 0);
+cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r = 0);
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r = 0);
 
 struct RescoreArgs {
   const int64_t* row_ptr;
@@ -158,6 +169,14 @@ struct IvfBuildArgs {
   int32_t* toff;         // or null
   int32_t n_tiles_max, k_tile;
   int64_t* d_e;          // [1] receives E
+  // dense head rows (null head_slot = off; single-instance contexts only)
+  int32_t* head_slot;    // [Dt]
+  void* wd;              // [head_max * kpad]
+  int64_t kpad;
+  int64_t head_max;      // rows available in wd
+  int64_t head_min_nc;   // a list of at least this many clusters is stored densely
+  uint32_t* hflags;      // [Dt+1] scratch
+  int64_t* d_heads;      // [1] receives the number of dense rows
   // scratch
   uint32_t* k32a;
   uint32_t* k32b;
@@ -168,6 +187,7 @@ struct IvfBuildArgs {
 };
 cudaError_t launch_build_ivf(const IvfBuildArgs& a, cudaStream_t s);
 cudaError_t launch_build_toff(const IvfBuildArgs& a, cudaStream_t s);
+cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s);
 
 // Means from rows: validate cluster-major rows, fill the row owner of every
 // entry and (normalise != 0) divide each row by its FP64 L2 norm in place;

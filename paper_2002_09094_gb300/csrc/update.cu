@@ -148,26 +148,42 @@ __global__ void k_uptr(UpdateArgs a) {
     a.uptr[j] = lower_bound_dev<uint64_t>(a.ukey, u_n, (uint64_t)j << a.tbits);
 }
 
-// Thread per cluster: ||s_j||^2 in ascending term order, count of nonzero
-// elements, and the length of the new mean row.
+// Warp per cluster: ||s_j||^2 in ascending term order, count of nonzero
+// elements, and the length of the new mean row.  Lanes load and square 32
+// consecutive sums; the additions then run in the same sequential order as a
+// one-thread loop (every lane walks the same shuffled chain), so the result
+// does not depend on the launch shape.
 __global__ void k_cluster_norm(UpdateArgs a) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < a.kt; j += stride) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = gw; j < a.kt; j += nw) {
+    const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
     double n2 = 0.0;
-    int64_t nz = 0;
-    for (int64_t u = a.uptr[j]; u < a.uptr[j + 1]; ++u) {
-      const double s = a.usum[u];
-      n2 = __dadd_rn(n2, __dmul_rn(s, s));
-      nz += (s != 0.0) ? 1 : 0;
+    int nz = 0;
+    for (int64_t ub = u0; ub < u1; ub += 32) {
+      const int64_t u = ub + lane;
+      double sq = 0.0;
+      if (u < u1) {
+        const double s = a.usum[u];
+        sq = __dmul_rn(s, s);
+        nz += (s != 0.0) ? 1 : 0;
+      }
+      const int cnt = (int)min((int64_t)32, u1 - ub);
+      for (int q = 0; q < cnt; ++q) n2 = __dadd_rn(n2, __shfl_sync(IVF_FULL_MASK, sq, q));
     }
-    const double nrm = __dsqrt_rn(n2);
-    a.sum_norm[j] = nrm;
-    int64_t len;
-    if (nrm > 0.0)
-      len = nz;
-    else
-      len = a.empty_policy == 0 ? (a.mptr_old[j + 1] - a.mptr_old[j]) : 0;
-    a.newlen[j] = len;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(IVF_FULL_MASK, nz, o);
+    if (lane == 0) {
+      const double nrm = __dsqrt_rn(n2);
+      a.sum_norm[j] = nrm;
+      int64_t len;
+      if (nrm > 0.0)
+        len = nz;
+      else
+        len = a.empty_policy == 0 ? (a.mptr_old[j + 1] - a.mptr_old[j]) : 0;
+      a.newlen[j] = len;
+    }
   }
 }
 
@@ -270,6 +286,54 @@ __global__ void k_toff(IvfBuildArgs a) {
         hi = mid;
     }
     a.toff[x] = (int32_t)(lo - tb);
+  }
+}
+
+// ------------------------------------------------ dense head rows (IFN form)
+
+// A term whose posting list holds at least head_min_nc clusters is stored as
+// a dense row of kpad values (zeros where the list has no entry): the
+// paper's full inverted file (IFN) restricted to the densest lists.
+__global__ void k_head_flags(IvfBuildArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.dt; p += stride)
+    a.hflags[p] = (a.term_ptr[p + 1] - a.term_ptr[p] >= a.head_min_nc) ? 1u : 0u;
+}
+
+__global__ void k_head_slots(IvfBuildArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.dt; p += stride) {
+    const uint32_t s = a.hflags[p];
+    const bool head = a.hflags[p + 1] != s && (int64_t)s < a.head_max;
+    a.head_slot[p] = head ? (int32_t)s : -1;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t tot = (int64_t)a.hflags[a.dt];
+    *a.d_heads = tot < a.head_max ? tot : a.head_max;
+  }
+}
+
+template <typename WT>
+__global__ void k_head_zero(IvfBuildArgs a) {
+  WT* wd = static_cast<WT*>(a.wd);
+  const int64_t n = *a.d_heads * a.kpad;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) wd[x] = from_f32<WT>(0.f);
+}
+
+// Warp per term: copy a head term's list into its dense row.
+template <typename WT>
+__global__ void k_head_fill(IvfBuildArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  WT* wd = static_cast<WT*>(a.wd);
+  const WT* w = static_cast<const WT*>(a.w);
+  for (int64_t p = gw; p < a.dt; p += nw) {
+    const int32_t s = a.head_slot[p];
+    if (s < 0) continue;
+    WT* row = wd + (int64_t)s * a.kpad;
+    for (int64_t q = a.term_ptr[p] + lane; q < a.term_ptr[p + 1]; q += 32) row[a.cid32[q]] = w[q];
   }
 }
 
@@ -404,7 +468,7 @@ cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
   const unsigned gK = grid_for(a.kt + 1, T256, 8192);
   k_uptr<<<gK, T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
-  k_cluster_norm<<<grid_for(a.kt, 64, 8192), 64, 0, s>>>(a);
+  k_cluster_norm<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
   k_write_means<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
@@ -435,6 +499,37 @@ cudaError_t launch_build_ivf(const IvfBuildArgs& a, cudaStream_t s) {
   }
   IVF_LAUNCH_CHECK();
   if (a.toff) IVF_CU(launch_build_toff(a, s));
+  if (a.head_slot) IVF_CU(launch_build_head(a, s));
+  return cudaSuccess;
+}
+
+cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s) {
+  const unsigned gD = grid_for(a.dt, T256, 16384);
+  k_head_flags<<<gD, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_u32(a.hflags, a.hflags, a.dt, a.temp, s));
+  k_head_slots<<<gD, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  const unsigned gW = grid_for(a.head_max * a.kpad, T256, 16384);
+  const unsigned gF = grid_for(a.dt * 32, T256, 16384);
+  switch (a.storage) {
+    case ST_F16:
+      k_head_zero<__half><<<gW, T256, 0, s>>>(a);
+      IVF_LAUNCH_CHECK();
+      k_head_fill<__half><<<gF, T256, 0, s>>>(a);
+      break;
+    case ST_BF16:
+      k_head_zero<__nv_bfloat16><<<gW, T256, 0, s>>>(a);
+      IVF_LAUNCH_CHECK();
+      k_head_fill<__nv_bfloat16><<<gF, T256, 0, s>>>(a);
+      break;
+    default:
+      k_head_zero<float><<<gW, T256, 0, s>>>(a);
+      IVF_LAUNCH_CHECK();
+      k_head_fill<float><<<gF, T256, 0, s>>>(a);
+      break;
+  }
+  IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }
 

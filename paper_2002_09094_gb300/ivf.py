@@ -25,6 +25,9 @@ STATUS_NAMES = {0: "IVF_OK", 1: "IVF_E_INVALID", 2: "IVF_E_STATE", 3: "IVF_E_OOM
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 IVF_FLAG_VALIDATE = 1
 IVF_FLAG_NO_GRAPH = 2
+IVF_FLAG_DENSE_HEAD = 4
+IVF_FLAG_SPARSE_ONLY = 8
+KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG_SPARSE_ONLY}
 
 # Every symbol include/ivf.h declares.
 EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_from_docs", "ivf_assign",
@@ -71,7 +74,9 @@ class Info(ctypes.Structure):
     _fields_ = [("n_docs", ctypes.c_int64), ("n_terms", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("n_instances", ctypes.c_int32), ("ivf_entries", ctypes.c_int64),
                 ("ivf_capacity", ctypes.c_int64), ("k_tile", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("iteration", ctypes.c_int32), ("storage", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("iteration", ctypes.c_int32), ("storage", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("dense_head_r", ctypes.c_int32), ("dense_head_theta", ctypes.c_float),
+                ("dense_head_rows", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -164,7 +169,7 @@ class IVF:
 
     def __init__(self, row_ptr, term, val, n_terms: int, k: int, storage: str = "f32", rescore: bool = True,
                  empty_policy: int = 0, k_tile: int = 0, warps_per_block: int = 0, validate: bool = False,
-                 use_graph: bool = True, stream=None, _batched=None):
+                 use_graph: bool = True, stream=None, kernel: str = "auto", _batched=None):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p(0)
         rp, rk = _ptr(row_ptr, np.int64)
@@ -172,7 +177,7 @@ class IVF:
         vptr, vk = _ptr(val, np.float32)
         n_docs = int(len(row_ptr) - 1)
         nnz = int(len(term))
-        flags = (IVF_FLAG_VALIDATE if validate else 0) | (0 if use_graph else IVF_FLAG_NO_GRAPH)
+        flags = (IVF_FLAG_VALIDATE if validate else 0) | (0 if use_graph else IVF_FLAG_NO_GRAPH) | KERNEL_FLAGS[kernel]
         cfg = Config(n_docs=n_docs, n_terms=int(n_terms), nnz=nnz, k=int(k), storage=STORAGE[storage],
                      rescore=1 if rescore else 0, empty_policy=int(empty_policy), k_tile=int(k_tile),
                      warps_per_block=int(warps_per_block), flags=flags, reserved=0)

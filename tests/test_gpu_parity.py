@@ -411,3 +411,60 @@ def test_large_k_tiled_sampled_lockstep():
     reps = lockstep(c, w.k, ids, 2, rows=rows)
     for rep in reps:
         assert_report_ok(rep, check_objective=False)
+
+
+# ------------------------------------------------ dense-head kernel (IFN rows)
+
+
+@pytest.mark.parametrize("kernel", ["dense_head", "sparse"])
+def test_kernel_family_lockstep_small_workload(kernel):
+    """Both kernel families meet the bar on the 10k-doc workload, and the
+    dense-head kernel really stores dense rows there."""
+    w = dg.SMALL
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    reps = lockstep(c, w.k, ids, 5, kernel=kernel)
+    for rep in reps:
+        assert_report_ok(rep)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, kernel=kernel) as m:
+        m.set_means_from_docs(ids)
+        m.iterate(3)
+        info = m.info()
+    if kernel == "dense_head":
+        assert info["dense_head_r"] > 0 and info["dense_head_rows"] > 0
+    else:
+        assert info["dense_head_r"] == 0
+
+
+@pytest.mark.parametrize("k", [700, 3000, 5000])
+def test_dense_head_tiled_lockstep(k):
+    c = corpus_for(8000, 6000, mean_len=45.0, seed=k + 1)
+    ids = dg.init_doc_ids(c.n_docs, k, k + 1)
+    reps = lockstep(c, k, ids, 3, kernel="dense_head")
+    for rep in reps:
+        assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 3e-3), ("bf16", 2.5e-2)])
+def test_dense_head_mixed_precision(storage, tol):
+    c = corpus_for(6000, 8000, mean_len=40.0, seed=23)
+    k = 1500
+    ids = dg.init_doc_ids(c.n_docs, k, 23)
+    for rep in lockstep(c, k, ids, 3, storage=storage, best_tol=tol, kernel="dense_head"):
+        assert_report_ok(rep)
+
+
+def test_dense_head_and_sparse_kernels_agree():
+    c = corpus_for(5000, 5000, mean_len=40.0, seed=24)
+    k = 2000
+    ids = dg.init_doc_ids(c.n_docs, k, 24)
+    out = {}
+    for kernel in ("dense_head", "sparse"):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel=kernel) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(3)
+            st = m.assign()
+            out[kernel] = (m.get_assign(), m.get_best(), st["entries_visited"])
+    assert np.array_equal(out["dense_head"][0], out["sparse"][0])
+    assert np.allclose(out["dense_head"][1], out["sparse"][1], rtol=0, atol=1e-6)
+    assert out["dense_head"][2] == out["sparse"][2]
