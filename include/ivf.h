@@ -234,6 +234,51 @@ ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* ins
 /* Per-instance change counts of the last assignment: int64[n_inst] (host or device). */
 ivf_status ivfb_get_changed(ivf_ctx* ctx, int64_t* out);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free assignment step.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory where they run
+ * the assignment -- applications whose device memory is owned by their own
+ * pool or framework allocator, latency-critical loops that must not pay for
+ * (or synchronise the device on) a cudaMalloc after start-up, and services
+ * that reserve all memory once.  It allocates nothing: no cudaMalloc, no
+ * cudaFree, no allocating library routine, and no context.
+ *
+ * The caller passes every input and output as DEVICE pointers:
+ *   objects: row_ptr int64[N+1], term int32[nnz], val float[nnz] (CSR, as
+ *     for ivf_create);
+ *   the inverted file of the means: term_ptr int64[D+1], cid int32[E]
+ *     (cluster ids, ascending inside each term's list), w float[E];
+ *   the FP64 means it was cast from, cluster-major: mean_ptr int64[K+1],
+ *     mean_term int32[E], mean_val double[E] (ivf_get_inverted_file and
+ *     ivf_get_means return exactly these);
+ *   outputs: assign_out int32[N], best_out float[N] or NULL, gap_out float[N]
+ *     or NULL.
+ * The result equals ivf_assign's on a context with FP32 storage and
+ * rescore = 1: the FP64 argmax (lowest cluster id on ties), the FP32 best
+ * similarity, and the top-2 gap.
+ *
+ * The call's scratch -- work counters, object norms, and the queue of
+ * near-tie objects for the FP64 re-score -- lives in one file-scope static
+ * device array of IVF_STATIC_SCRATCH_BYTES bytes; every GPU that loads this
+ * library holds it until the process exits.  Sizes beyond the limits
+ * (N > IVF_STATIC_MAX_DOCS, K > IVF_STATIC_MAX_K, K > N) return
+ * IVF_E_INVALID before any GPU work; a failing CUDA call returns IVF_E_CUDA.
+ * The first call on a device does a one-time set-up there (it looks up the
+ * scratch array's device address with cudaGetSymbolAddress and raises the
+ * kernel's shared-memory limit); make that first call before any stream
+ * capture.  All calls share the one array, which keeps the last call's
+ * contents (each call clears what must start at zero): calls that overlap
+ * on the GPU -- from two streams or two threads -- race, so the caller must
+ * serialise them. */
+#define IVF_STATIC_MAX_DOCS 16384
+#define IVF_STATIC_MAX_K 12288
+#define IVF_STATIC_SCRATCH_BYTES 2425088
+ivf_status ivf_assign_static(int64_t n_docs, const int64_t* row_ptr, const int32_t* term, const float* val,
+                             int64_t n_terms, int32_t k, const int64_t* term_ptr, const int32_t* cid,
+                             const float* w, const int64_t* mean_ptr, const int32_t* mean_term,
+                             const double* mean_val, int32_t* assign_out, float* best_out, float* gap_out,
+                             void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -525,6 +525,25 @@ cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream
   return cudaSuccess;
 }
 
+cudaError_t assign_prepare_i32ids(int tile_cap, int warps) {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_assign<float, int32_t, 0>),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)assign_smem_bytes(tile_cap, warps));
+}
+
+int assign_max_blocks_per_sm_i32ids(int tile_cap, int warps) {
+  int nb = 0;  // the shared-memory limit was raised once at set-up (assign_prepare_i32ids)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, reinterpret_cast<const void*>(&k_assign<float, int32_t, 0>),
+                                                    warps * 32, assign_smem_bytes(tile_cap, warps)) != cudaSuccess)
+    return 0;
+  return nb;
+}
+
+cudaError_t launch_assign_i32ids(const AssignArgs& a, int warps, int blocks, cudaStream_t s) {
+  k_assign<float, int32_t, 0><<<blocks, warps * 32, assign_smem_bytes(a.tile_cap, warps), s>>>(a);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
 cudaError_t launch_rescore(const RescoreArgs& a, int blocks, cudaStream_t s) {
   k_rescore<<<blocks, 256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();

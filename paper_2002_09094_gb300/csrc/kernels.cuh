@@ -64,6 +64,10 @@ size_t assign_smem_bytes(int tile_cap, int warps);
 cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r = 0);
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r = 0);
 int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r = 0);
+// FP32 storage, untiled, int32 cluster ids (the caller-held inverted file of ivf_assign_static).
+cudaError_t assign_prepare_i32ids(int tile_cap, int warps);
+int assign_max_blocks_per_sm_i32ids(int tile_cap, int warps);
+cudaError_t launch_assign_i32ids(const AssignArgs& a, int warps, int blocks, cudaStream_t s);
 
 struct RescoreArgs {
   const int64_t* row_ptr;

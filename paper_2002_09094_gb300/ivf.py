@@ -34,7 +34,9 @@ EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_fro
            "ivf_update", "ivf_iterate", "ivf_get_assign", "ivf_get_best", "ivf_get_gap", "ivf_get_info",
            "ivf_get_means", "ivf_get_inverted_file", "ivf_get_members", "ivf_set_assign", "ivf_restore_means",
            "ivf_last_error", "ivf_destroy", "ivf_launch_count", "ivf_version", "ivfb_create", "ivfb_get_changed",
-           "ivf_timing_reset", "ivf_get_timing"]
+           "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static"]
+IVF_STATIC_MAX_DOCS = 16384
+IVF_STATIC_MAX_K = 12288
 
 
 class IvfError(RuntimeError):
@@ -120,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ivfb_get_changed": ([vp, vp], st),
         "ivf_timing_reset": ([vp, i32], st),
         "ivf_get_timing": ([vp, P(Timing)], st),
+        "ivf_assign_static": ([i64, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
