@@ -49,6 +49,7 @@ def parse():
                    "(same generator; for small profiling cases)")
     p.add_argument("--kernel", choices=["auto", "dense_head", "sparse"], default="auto",
                    help="assignment kernel family (auto = the autotuner picks)")
+    p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -373,11 +374,85 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_batched(args, rank, world, local):
+    """Many independent instances of uneven N, K and D in one context: one
+    launch per phase for all of them and CUDA-graph iterations, against the
+    same instances run one after the other in their own contexts."""
+    import torch
+
+    from paper_2002_09094_gb300 import build as cuda_build
+    from paper_2002_09094_gb300 import datagen as dg
+    from paper_2002_09094_gb300 import ivf
+
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    ws = dg.batched_workloads(n_instances=args.instances)
+    t0 = time.time()
+    cs = [dg.make_corpus(w.corpus) for w in ws]
+    gen_s = time.time() - t0
+    ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
+    inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
+    offs = np.concatenate([[0], np.cumsum([c.nnz for c in cs])]).astype(np.int64)
+    row_ptr = np.concatenate([c.row_ptr[:-1] + o for c, o in zip(cs, offs)] + [offs[-1:]]).astype(np.int64)
+    term = np.concatenate([c.term for c in cs])
+    val = np.concatenate([c.val for c in cs])
+    iters = args.steps
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        m = ivf.BatchedIVF(row_ptr, term, val, inst_docs, [c.n_terms for c in cs], [w.k for w in ws],
+                           storage=args.storage, stream=stream.cuda_stream)
+        del term, val
+        m.set_means_from_docs(np.concatenate(ids))
+        m.iterate(args.warmup)
+        launches0 = ivf.launch_count()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        done, conv, st = m.iterate(iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batched_ms = e0.elapsed_time(e1) / max(1, done)
+        launches = ivf.launch_count() - launches0
+        a_batched = m.get_assign()
+        info = m.info()
+        m.close()
+        # the same instances, one context each, same iterations
+        seq_ms = 0.0
+        equal = True
+        for b, (w, c, d) in enumerate(zip(ws, cs, ids)):
+            with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage,
+                         stream=stream.cuda_stream) as s1:
+                s1.set_means_from_docs(d)
+                s1.iterate(args.warmup)
+                torch.cuda.synchronize()
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                s1.iterate(done)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                seq_ms += f0.elapsed_time(f1) / max(1, done)
+                equal &= bool(np.array_equal(s1.get_assign(), a_batched[inst_docs[b]:inst_docs[b + 1]]))
+    out = {"metric": METRIC, "value": batched_ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": int(done),
+           "warmup": args.warmup, "ms_per_step": round(batched_ms, 4), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
+           "data": "synthetic", "impl": "ours",
+           "config": {"workload": f"batched-{args.instances}-instances", "instances": args.instances,
+                      "n_docs": int(inst_docs[-1]), "nnz": int(offs[-1]), "k_total": int(sum(w.k for w in ws)),
+                      "storage": args.storage, "iterations": "graph-captured", "generation_s": round(gen_s, 1),
+                      "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"]},
+           "sequential_s_per_iter": seq_ms / 1e3, "batched_speedup": round(seq_ms / batched_ms, 3),
+           "equal_assignments": equal, "converged": bool(conv), "gpu_launches": int(launches)}
+    if rank == 0:
+        emit(out)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

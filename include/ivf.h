@@ -83,7 +83,8 @@ typedef struct {
                           else a power of two in [512, 65536] or >= k (no tiling) */
   int32_t warps_per_block; /* 0 = autotune, else 1..32 */
   uint32_t flags;      /* IVF_FLAG_* */
-  int32_t reserved;
+  int32_t means_capacity; /* entries reserved for the means / inverted file at create
+                             (0 = automatic); the arrays grow on demand */
 } ivf_config;
 
 /* Per-iteration statistics (Section 5.2 reports time and memory per
@@ -156,7 +157,9 @@ ivf_status ivf_assign(ivf_ctx* ctx, int32_t* assign_out, float* best_out, float*
                       ivf_iter_stats* stats_out);
 
 /* Update step of Algorithm 3 from the last assignment: member sums in FP64,
- * L2 normalisation, inverted-file rebuild. */
+ * L2 normalisation, inverted-file rebuild.  Synchronises the stream once to
+ * check that the new means fit; if not, it grows the arrays and redoes the
+ * step (IVF_E_OOM if the device has no room). */
 ivf_status ivf_update(ivf_ctx* ctx);
 
 /* Run assignment + update until no assignment changes (from the second

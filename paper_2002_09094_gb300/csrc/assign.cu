@@ -79,54 +79,117 @@ __device__ __forceinline__ int find_instance(const int64_t* offs, int n_inst, in
 //   FP16/BF16: both operands rounded (u' = u16 + 2u for the FP64->FP32->16
 //   double rounding), products exact in FP32, plus the FP16 subnormal floor
 //   and gamma_m on the summed magnitudes.
-__device__ __forceinline__ float err_bound(int m, float nx, int storage) {
+//   With every object value and mean value >= 0 the products are all >= 0,
+//   so sum_h |v u| is rho itself and the bound scales with the similarity:
+//   E(rho_hat) = rel * rho_hat + abs (P = exact sum of the stored products,
+//   c = per-product relative error: |rho_hat - P| <= gamma P,
+//   |P - rho| <= c rho + sub, rho <= (P + sub)/(1 - c), P <= rho_hat/(1 - gamma)).
+//   Otherwise E is the constant S-based bound (rel = 0).
+struct ErrBound {
+  float rel, abs;
+  __device__ __forceinline__ float e2(float rho_hat) const { return 2.f * (rel * fmaxf(rho_hat, 0.f) + abs); }
+};
+
+__device__ __forceinline__ ErrBound err_bound(int m, float nx, int storage, bool nonneg) {
   const float u32 = 5.9604645e-08f;  // 2^-24
-  const float S = nx * 1.000001f;
   const float fm = (float)m;
   // m + 1 roundings at most per rho_c: up to m FMAs in the head and tail
   // chains together, plus the one addition that joins them
   const float g = (fm + 1.f) * u32 / (1.f - (fm + 1.f) * u32);
-  float e;
+  float c, sub;
   if (storage == ST_F32) {
-    e = S * (u32 + g * (1.f + u32));
+    c = u32;           // the mean's rounding to FP32; object values are exact
+    sub = fm * 1e-37f;  // FP32 subnormal floor (negligible)
   } else {
     const float u16 = storage == ST_F16 ? 4.8828125e-04f : 3.90625e-03f;
     const float up = u16 + 2.f * u32;
-    const float sub = storage == ST_F16 ? fm * u32 * (1.f + up) : fm * 1e-37f;
-    const float mag = S * (1.f + up) * (1.f + up) + sub;
-    e = S * (2.f * up + up * up) + sub + g * mag;
+    c = 2.f * up + up * up;
+    sub = storage == ST_F16 ? fm * u32 * (1.f + up) : fm * 1e-37f;
   }
-  return e * 1.0001f;
+  ErrBound b;
+  if (nonneg) {
+    b.rel = (g + c / (1.f - c)) / (1.f - g) * 1.0001f;
+    b.abs = sub / (1.f - c) * 1.0001f;
+  } else {
+    const float S = nx * 1.000001f;
+    float e;
+    if (storage == ST_F32)
+      e = S * (u32 + g * (1.f + u32));
+    else
+      e = S * c + sub + g * (S * (1.f + c) + sub);
+    b.rel = 0.f;
+    b.abs = e * 1.0001f;
+  }
+  return b;
 }
 
 // Drop candidates below thr (warp-cooperative, ncand uniform across lanes).
+// Compaction only moves entries to lower positions, chunk by chunk.
 __device__ __forceinline__ void prune_candidates(int* cand_id, float* cand_val, int& ncand, float thr, int lane) {
-  if (ncand == 0) return;
-  int idv = 0;
-  float vv = -INFINITY;
-  bool keep = false;
-  if (lane < ncand) {
-    idv = cand_id[lane];
-    vv = cand_val[lane];
-    keep = vv >= thr;
+  int out = 0;
+  for (int base = 0; base < ncand; base += 32) {
+    const int q = base + lane;
+    int idv = 0;
+    float vv = -INFINITY;
+    bool keep = false;
+    if (q < ncand) {
+      idv = cand_id[q];
+      vv = cand_val[q];
+      keep = vv >= thr;
+    }
+    const unsigned km = __ballot_sync(IVF_FULL_MASK, keep);
+    __syncwarp();
+    if (keep) {
+      const int pos = out + __popc(km & ((1u << lane) - 1u));
+      cand_id[pos] = idv;
+      cand_val[pos] = vv;
+    }
+    out += __popc(km);
+    __syncwarp();
   }
-  const unsigned km = __ballot_sync(IVF_FULL_MASK, keep);
-  __syncwarp();
-  if (keep) {
-    const int pos = __popc(km & ((1u << lane) - 1u));
-    cand_id[pos] = idv;
-    cand_val[pos] = vv;
+  ncand = out;
+}
+
+// 16 bytes of a dense head row -> floats.
+template <typename WT>
+__device__ __forceinline__ void unpack16(uint4 raw, float* e);
+template <>
+__device__ __forceinline__ void unpack16<float>(uint4 raw, float* e) {
+  e[0] = __uint_as_float(raw.x);
+  e[1] = __uint_as_float(raw.y);
+  e[2] = __uint_as_float(raw.z);
+  e[3] = __uint_as_float(raw.w);
+}
+template <>
+__device__ __forceinline__ void unpack16<__half>(uint4 raw, float* e) {
+  const uint32_t u[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __half2_raw hr;
+    hr.x = (unsigned short)(u[q] & 0xFFFFu);
+    hr.y = (unsigned short)(u[q] >> 16);
+    const float2 f = __half22float2(__half2(hr));
+    e[2 * q] = f.x;
+    e[2 * q + 1] = f.y;
   }
-  ncand = __popc(km);
-  __syncwarp();
+}
+template <>
+__device__ __forceinline__ void unpack16<__nv_bfloat16>(uint4 raw, float* e) {
+  const uint32_t u[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {  // a bf16 is the top half of an FP32
+    e[2 * q] = __uint_as_float(u[q] << 16);
+    e[2 * q + 1] = __uint_as_float(u[q] & 0xFFFF0000u);
+  }
 }
 
 // R > 0: hybrid kernel.  Posting lists stored as dense head rows are
-// accumulated in registers -- lane l owns clusters l, l+32, ..., l+32(R-1) of
-// the tile (tile = 32R clusters) -- so they need neither cluster ids nor
-// shared-memory read-modify-writes; the remaining (sparse) lists scatter into
-// the shared-memory tile as in the R = 0 kernel.  Per cluster the head and
-// the tail contributions are each summed in ascending term order, then added.
+// accumulated in registers -- with VEC values per 16-byte load, lane l owns
+// clusters VEC*(32g + l) + k of the tile (g < R/VEC, k < VEC; tile = 32R
+// clusters) -- so they need neither cluster ids nor shared-memory
+// read-modify-writes; the remaining (sparse) lists scatter into the
+// shared-memory tile as in the R = 0 kernel.  Per cluster the head and the
+// tail contributions are each summed in ascending term order, then added.
 template <typename WT, typename IdT, int R>
 __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assign(const AssignArgs a) {
   extern __shared__ __align__(16) float smem[];
@@ -140,6 +203,8 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
   const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
   const int32_t* __restrict__ head_slot = a.head_slot;
   constexpr int RR = R > 0 ? R : 1;
+  constexpr int VEC = 16 / (int)sizeof(WT);      // values per 16-byte load of a dense head row
+  constexpr int NG = RR >= VEC ? RR / VEC : 1;  // 16-byte groups per lane: clusters VEC*(32g + lane) + k
   float acc[RR];
   const int cmask = a.tiled ? (a.k_tile - 1) : 0xFFFF;
   const unsigned lt = (1u << lane) - 1u;
@@ -155,13 +220,14 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
     const int K = a.inst_clu[b + 1] - a.inst_clu[b];
     const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
     const int m = (int)(r1 - r0);
-    const float e2 = a.rescore ? 2.f * err_bound(m, a.nx[i], a.storage) : -1.f;
+    const ErrBound bound = err_bound(m, a.nx[i], a.storage, a.nonneg != 0);
     const int tile = a.tiled ? a.k_tile : K;
     const int n_tiles = a.tiled ? (K + a.k_tile - 1) / a.k_tile : 1;
     float best = -INFINITY, second = -INFINITY;
     int bid = 0x7fffffff;
     int ncand = 0;
     bool overflow = false;
+    const unsigned long long entries_before = my_entries;
 
     for (int tt = 0; tt < n_tiles; ++tt) {
       const int lo = tt * tile;
@@ -184,7 +250,10 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
           v = to_f32(val[h]);
           if (R > 0 && head_slot != nullptr) slot = __ldg(head_slot + t);
           const int64_t tb = __ldg(a.term_ptr + t);
-          if (a.tiled) {
+          if (slot >= 0) {
+            // a dense row covers every tile: its list length counts once (Eq. 15)
+            if (tt == 0) len = (int)(__ldg(a.term_ptr + t + 1) - tb);
+          } else if (a.tiled) {
             const int32_t* to = a.toff + (int64_t)t * (a.n_tiles_max + 1) + tt;
             const int o0 = __ldg(to), o1 = __ldg(to + 1);
             beg = tb + o0;
@@ -195,20 +264,51 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
           }
         }
         my_entries += (unsigned long long)len;
-        const int nh = (int)min((int64_t)32, r1 - h0);
-        for (int j = 0; j < nh; ++j) {
+        if constexpr (R > 0) {
+          // dense head rows of this chunk, two terms at a time (ascending term
+          // order per cluster): acc[g*VEC+k] += v * w[lo + VEC*(32g + lane) + k]
+          unsigned hm = __ballot_sync(IVF_FULL_MASK, slot >= 0);
+          while (hm) {
+            const int j0 = __ffs(hm) - 1;
+            hm &= hm - 1;
+            const bool two = hm != 0;
+            const int j1 = two ? __ffs(hm) - 1 : j0;
+            if (two) hm &= hm - 1;
+            const int s0 = __shfl_sync(IVF_FULL_MASK, slot, j0);
+            const int s1 = __shfl_sync(IVF_FULL_MASK, slot, j1);
+            const float v0 = __shfl_sync(IVF_FULL_MASK, v, j0);
+            const float v1 = two ? __shfl_sync(IVF_FULL_MASK, v, j1) : 0.f;  // fma(0, w, acc) == acc
+            const uint4* __restrict__ row0 = reinterpret_cast<const uint4*>(wd + (int64_t)s0 * a.kpad + lo) + lane;
+            const uint4* __restrict__ row1 = reinterpret_cast<const uint4*>(wd + (int64_t)s1 * a.kpad + lo) + lane;
+            uint4 w0[NG], w1[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g) w0[g] = __ldg(row0 + 32 * g);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) w1[g] = __ldg(row1 + 32 * g);
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              float e[VEC];
+              unpack16<WT>(w0[g], e);
+#pragma unroll
+              for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = fmaf(v0, e[k], acc[g * VEC + k]);
+            }
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              float e[VEC];
+              unpack16<WT>(w1[g], e);
+#pragma unroll
+              for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = fmaf(v1, e[k], acc[g * VEC + k]);
+            }
+          }
+        }
+        // sparse lists of this chunk, one at a time
+        unsigned tm = __ballot_sync(IVF_FULL_MASK, h < r1 && slot < 0);
+        while (tm) {
+          const int j = __ffs(tm) - 1;
+          tm &= tm - 1;
           const int64_t bj = __shfl_sync(IVF_FULL_MASK, beg, j);
           const int lj = __shfl_sync(IVF_FULL_MASK, len, j);
           const float vj = __shfl_sync(IVF_FULL_MASK, v, j);
-          if (R > 0) {
-            const int sj = __shfl_sync(IVF_FULL_MASK, slot, j);
-            if (sj >= 0) {  // dense head row: acc[r] += v * w[lo + lane + 32 r]
-              const WT* __restrict__ row = wd + (int64_t)sj * a.kpad + lo + lane;
-#pragma unroll
-              for (int r = 0; r < RR; ++r) acc[r] = fmaf(vj, to_f32(__ldg(row + 32 * r)), acc[r]);
-              continue;
-            }
-          }
           const IdT* __restrict__ cp = cid + bj;
           const WT* __restrict__ wp = w + bj;
           int q = lane;
@@ -236,14 +336,27 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
       // argmax over the tile: lowest id among the maxima, plus the runner-up
       float tb = -INFINITY, ts = -INFINITY;
       int ti = 0x7fffffff;
-      if (R > 0) {  // rho_c = head part (registers) + tail part (shared memory)
+      if constexpr (R > 0) {  // rho_c = head part (registers) + tail part (shared memory)
 #pragma unroll
-        for (int r = 0; r < RR; ++r) {
-          const int q = lane + 32 * r;
-          if (q < cnt) {
-            const float x = acc[r] + rho[q];
-            rho[q] = x;
-            top2_push(tb, ti, ts, x, lo + q);
+        for (int g = 0; g < NG; ++g) {
+#pragma unroll
+          for (int k4 = 0; k4 < VEC; k4 += 4) {
+            const int q0 = VEC * 32 * g + VEC * lane + k4;  // 16-byte aligned, < tile_cap
+            float4 t4 = *reinterpret_cast<const float4*>(rho + q0);
+            float x[4] = {acc[g * VEC + k4] + t4.x, acc[g * VEC + k4 + 1] + t4.y, acc[g * VEC + k4 + 2] + t4.z,
+                          acc[g * VEC + k4 + 3] + t4.w};
+            if (q0 + 3 < cnt) {
+              *reinterpret_cast<float4*>(rho + q0) = make_float4(x[0], x[1], x[2], x[3]);
+#pragma unroll
+              for (int k = 0; k < 4; ++k) top2_push(tb, ti, ts, x[k], lo + q0 + k);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                if (q0 + k < cnt) {
+                  rho[q0 + k] = x[k];
+                  top2_push(tb, ti, ts, x[k], lo + q0 + k);
+                }
+            }
           }
         }
       } else {
@@ -251,8 +364,8 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
       }
       warp_top2(tb, ti, ts);
       top2_merge(best, bid, second, tb, ti, ts);
-      if (e2 >= 0.f) {
-        const float thr = best - e2;
+      if (a.rescore) {
+        const float thr = best - bound.e2(best);
         prune_candidates(cand_id, cand_val, ncand, thr, lane);
         if (ts >= thr) {
           for (int q0 = 0; q0 < cnt; q0 += 32) {
@@ -294,16 +407,22 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
       a.best[i] = best;
       a.gap[i] = g;
     }
-    if (e2 >= 0.f && g <= e2) {
+    // An object that met no posting entry has rho = 0 exactly for every
+    // cluster: its lowest-id argmax is exact and needs no re-score.
+    const bool any_entry = __any_sync(IVF_FULL_MASK, my_entries != entries_before);
+    const float e2 = bound.e2(best);
+    if (a.rescore && any_entry && g <= e2) {
       prune_candidates(cand_id, cand_val, ncand, best - e2, lane);
       unsigned slot = 0;
       if (lane == 0) slot = atomicAdd(a.n_flagged, 1u);
       slot = __shfl_sync(IVF_FULL_MASK, slot, 0);
+      if ((int64_t)slot >= a.cand_slots) overflow = true;
       if (lane == 0) {
         a.flag_obj[slot] = (int32_t)i;
         a.flag_cnt[slot] = overflow ? -1 : ncand;
       }
-      if (!overflow && lane < ncand) a.flag_cand[(int64_t)slot * CAND_MAX + lane] = cand_id[lane];
+      if (!overflow)
+        for (int q = lane; q < ncand; q += 32) a.flag_cand[(int64_t)slot * CAND_MAX + q] = cand_id[q];
     }
     __syncwarp();
   }

@@ -33,8 +33,10 @@ constexpr size_t kFlagObj = kNorms + 4ull * IVF_STATIC_MAX_DOCS;       // int32[
 constexpr size_t kFlagCnt = kFlagObj + 4ull * IVF_STATIC_MAX_DOCS;     // int32[MAX_DOCS]
 constexpr size_t kBest = kFlagCnt + 4ull * IVF_STATIC_MAX_DOCS;        // float[MAX_DOCS] when best_out is NULL
 constexpr size_t kGap = kBest + 4ull * IVF_STATIC_MAX_DOCS;            // float[MAX_DOCS] when gap_out is NULL
-constexpr size_t kFlagCand = kGap + 4ull * IVF_STATIC_MAX_DOCS;        // int32[MAX_DOCS * CAND_MAX]
-constexpr size_t kScratchBytes = kFlagCand + 4ull * IVF_STATIC_MAX_DOCS * CAND_MAX;
+constexpr size_t kFlagCand = kGap + 4ull * IVF_STATIC_MAX_DOCS;        // int32[kCandInts]
+constexpr size_t kCandInts = 32ull * IVF_STATIC_MAX_DOCS;               // candidate lists of kCandSlots objects
+constexpr int64_t kCandSlots = (int64_t)(kCandInts / CAND_MAX);        // later flagged objects: all clusters
+constexpr size_t kScratchBytes = kFlagCand + 4ull * kCandInts;
 static_assert(kScratchBytes == IVF_STATIC_SCRATCH_BYTES, "scratch size stated in ivf.h");
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
@@ -137,8 +139,10 @@ extern "C" ivf_status ivf_assign_static(int64_t n_docs, const int64_t* row_ptr, 
   k_static_setup<<<1, 32, 0, s>>>(scratch, n_docs, k, (int32_t)n_terms);
   note_launch();
   if (cudaGetLastError() != cudaSuccess) return IVF_E_CUDA;
+  // the sign flag is not read here: the call uses the bound valid for signed values
+  unsigned* negative = reinterpret_cast<unsigned*>(scratch + kTables + 128);
   if (launch_prepare_objects(n_docs, 0, 0, row_ptr, const_cast<int32_t*>(term), val, nullptr, ST_F32, nx, 1,
-                             tab->docs, tab->toff, tab->terms, 0, &ctr->status, s) != cudaSuccess)
+                             tab->docs, tab->toff, tab->terms, 0, &ctr->status, negative, s) != cudaSuccess)
     return IVF_E_CUDA;
 
   AssignArgs a{};
@@ -169,6 +173,8 @@ extern "C" ivf_status ivf_assign_static(int64_t n_docs, const int64_t* row_ptr, 
   a.flag_obj = flag_obj;
   a.flag_cnt = flag_cnt;
   a.flag_cand = flag_cand;
+  a.cand_slots = kCandSlots;
+  a.nonneg = 0;
   if (launch_assign_i32ids(a, warps, bps * sms, s) != cudaSuccess) return IVF_E_CUDA;
 
   RescoreArgs r{};

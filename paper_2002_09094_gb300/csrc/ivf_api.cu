@@ -40,6 +40,7 @@ struct DevCounters {
   unsigned long long acc_entries;   // timing window sums
   unsigned long long acc_rescored;
   long long heads;                  // dense head rows of the inverted file last built
+  unsigned int negative;            // some object value is negative (not an error)
 };
 
 struct Shape {
@@ -153,6 +154,9 @@ struct ivf_ctx {
   bool tuned_on_updated_means = false;  // the choice was made on means from an update step
   // state
   bool means_set = false;
+  bool objects_nonneg = true;  // every object value >= 0
+  bool means_nonneg = true;    // every mean value >= 0
+  int64_t cand_slots = 0;      // flagged objects with room for a candidate list
   int32_t iteration = 0;
   // graphs keyed by (mcur, alatest)
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -296,6 +300,16 @@ ivf_status check_status(ivf_ctx* c) {
   return IVF_OK;
 }
 
+// Whether every object value is >= 0 (then every mean built from objects is
+// too, and the assignment uses the similarity-relative error bound).
+ivf_status read_objects_sign(ivf_ctx* c) {
+  unsigned neg = 0;
+  CK(c, cudaMemcpyAsync(&neg, &c->dc->negative, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->objects_nonneg = neg == 0;
+  return IVF_OK;
+}
+
 // --------------------------------------------------------------- create
 
 ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vector<int64_t>& inst_docs,
@@ -383,7 +397,8 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->gap, N);
   AL(c->flag_obj, N);
   AL(c->flag_cnt, N);
-  AL(c->flag_cand, N * (int64_t)CAND_MAX);
+  c->cand_slots = std::min<int64_t>(N, int64_t(1) << 20);
+  AL(c->flag_cand, c->cand_slots * (int64_t)CAND_MAX);
   AL(c->dc, 1);
   c->d_e = reinterpret_cast<int64_t*>(&c->dc->ivf_e);
   c->red_blocks = (int)std::min<int64_t>(ceil_div(N, 256), 4 * (int64_t)c->num_sms);
@@ -414,7 +429,12 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
     e = cudaEventCreate(&ev);
     if (e != cudaSuccess) return bail(fail_cuda(c, "cudaEventCreate", e));
   }
-  if ((s = alloc_means(c, nnz + nnz / 4 + 4096)) != IVF_OK) return bail(s);
+  // The means rarely need more entries than half the tuples; very large
+  // problems start there and grow on demand (grow_means), smaller ones get room.
+  const int64_t cap0 = cfg->means_capacity > 0 ? (int64_t)cfg->means_capacity
+                       : nnz > (int64_t(400) << 20) ? nnz / 2 + 4096
+                                                     : nnz + nnz / 4 + 4096;
+  if ((s = alloc_means(c, cap0)) != IVF_OK) return bail(s);
   if ((s = alloc_scratch(c, std::max<int64_t>({nnz, c->cap, N, 1}))) != IVF_OK) return bail(s);
 
   cudaStream_t st = c->stream;
@@ -437,9 +457,10 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   CKB(launch_prepare_objects(N, nnz, 0, c->row_ptr, c->term, c->val32,
                              cfg->storage == IVF_F32 ? nullptr : c->val_store, cfg->storage, c->nx, n_inst,
                              c->inst_docs, c->inst_toff, c->inst_terms, (cfg->flags & IVF_FLAG_VALIDATE) ? 1 : 0,
-                             &c->dc->status, st));
+                             &c->dc->status, &c->dc->negative, st));
 #undef CKB
   if ((s = check_status(c)) != IVF_OK) return bail(s);
+  if ((s = read_objects_sign(c)) != IVF_OK) return bail(s);
   *out = c;
   return IVF_OK;
 }
@@ -450,6 +471,7 @@ ivf_status validate_cfg(const ivf_config* cfg) {
   if (cfg->empty_policy != 0 && cfg->empty_policy != 1) return IVF_E_INVALID;
   if (cfg->rescore != 0 && cfg->rescore != 1) return IVF_E_INVALID;
   if (cfg->warps_per_block < 0 || cfg->warps_per_block > 32) return IVF_E_INVALID;
+  if (cfg->means_capacity < 0) return IVF_E_INVALID;
   if (cfg->k_tile < 0) return IVF_E_INVALID;
   return IVF_OK;
 }
@@ -489,6 +511,8 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
     a.kpad = c->kpad;
     a.head_max = c->head_max;
     a.head_min_nc = std::max<int64_t>(1, (int64_t)std::ceil((double)c->shape.head_theta * c->kmax));
+    a.head_theta = c->shape.head_theta;
+    a.inst_toff = c->inst_toff;
     a.hflags = c->hflags;
     a.d_heads = reinterpret_cast<int64_t*>(&c->dc->heads);
   }
@@ -555,6 +579,8 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
   a.flag_obj = c->flag_obj;
   a.flag_cnt = c->flag_cnt;
   a.flag_cand = c->flag_cand;
+  a.cand_slots = c->cand_slots;
+  a.nonneg = (c->objects_nonneg && c->means_nonneg) ? 1 : 0;
   if (sh.head_r > 0) {
     a.head_slot = c->head_slot;
     a.wd = c->wd;
@@ -566,10 +592,7 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
 // head_r > 0 selects the dense-head kernel, whose tile is 32 * head_r clusters.
 bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f) {
   Shape sh;
-  if (head_r > 0) {
-    if (c->n_inst != 1) return false;
-    k_tile = 32 * head_r;
-  }
+  if (head_r > 0) k_tile = 32 * head_r;
   if (k_tile <= 0 || k_tile >= c->kmax) {
     if (c->kmax > 65536) return false;
     sh.tiled = 0;
@@ -581,6 +604,8 @@ bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0
     sh.k_tile = k_tile;
     sh.tile_cap = k_tile;
   }
+  // the dense-head kernel reads whole 16-byte groups of the 32R-cluster tile
+  if (head_r > 0) sh.tile_cap = 32 * head_r;
   sh.head_r = head_r;
   sh.head_theta = theta;
   const size_t per_warp = ((size_t)sh.tile_cap + 2 * CAND_MAX) * sizeof(float);
@@ -636,8 +661,11 @@ ivf_status autotune(ivf_ctx* c) {
         if (shape_for(c, 0, c->cfg.warps_per_block, &sh, hr, theta)) cands.push_back(sh);
   }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
+  // Contexts of the same shape in one process reuse the first choice, so
+  // their FP32 rounding (which depends on the kernel family) is the same.
+  const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY));
   auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
-                             (c->cfg.storage * 16 + (int)c->cfg.flags) * 2 + (c->iteration > 0 ? 1 : 0),
+                             (c->cfg.storage * 16 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
                              c->n_inst);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -837,9 +865,64 @@ ivf_status copy_mean_rows_in(ivf_ctx* c, const int64_t* mean_ptr, std::vector<in
   return IVF_OK;
 }
 
+// Grow the means / inverted-file arrays to new_cap entries, keeping the
+// current means (buffer mcur), which an update step still reads.
+ivf_status grow_means(ivf_ctx* c, int64_t new_cap) {
+  const int mb = c->mcur;
+  int64_t e_old = 0;
+  CK(c, cudaMemcpyAsync(&e_old, c->mptr[mb] + c->Kt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  int32_t* t_keep = nullptr;
+  double* v_keep = nullptr;
+  int32_t* cl_keep = nullptr;
+  ST(dalloc(c, &t_keep, new_cap));
+  ST(dalloc(c, &v_keep, new_cap));
+  ST(dalloc(c, &cl_keep, new_cap));
+  CK(c, cudaMemcpyAsync(t_keep, c->mterm[mb], sizeof(int32_t) * e_old, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(v_keep, c->mval[mb], sizeof(double) * e_old, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(cl_keep, c->mclu[mb], sizeof(int32_t) * e_old, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  void* old[] = {c->mterm[0], c->mterm[1], c->mval[0], c->mval[1], c->mclu[0], c->mclu[1], c->cid16, c->cid32, c->w};
+  for (void* p : old) dfree(c, p);
+  c->mterm[mb] = t_keep;
+  c->mval[mb] = v_keep;
+  c->mclu[mb] = cl_keep;
+  ST(dalloc(c, &c->mterm[mb ^ 1], new_cap));
+  ST(dalloc(c, &c->mval[mb ^ 1], new_cap));
+  ST(dalloc(c, &c->mclu[mb ^ 1], new_cap));
+  ST(dalloc(c, &c->cid16, new_cap + 8));
+  ST(dalloc(c, &c->cid32, new_cap));
+  char* wp = nullptr;
+  ST(dalloc(c, &wp, (new_cap + 8) * (int64_t)storage_bytes(c->cfg.storage)));
+  c->w = wp;
+  c->cap = new_cap;
+  if (std::max<int64_t>({c->nnz, c->cap, c->N, 1}) > c->scratch_len)
+    ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N, 1})));
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+// After an update step (means mcur -> mcur^1) whose new means did not fit
+// (STS_CAPACITY): grow and run the update again from the same assignment.
+// Synchronises.
+ivf_status redo_update_if_overflow(ivf_ctx* c, int src) {
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    unsigned st = 0;
+    int64_t e_new = 0;
+    CK(c, cudaMemcpyAsync(&st, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&e_new, c->mptr[c->mcur ^ 1] + c->Kt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (!(st & STS_CAPACITY)) return IVF_OK;
+    CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), c->stream));
+    ST(grow_means(c, e_new + e_new / 4 + 4096));
+    ST(enqueue_update(c, src));
+  }
+  return fail(c, IVF_E_OOM, "new means exceed the inverted-file capacity after growing it");
+}
+
 ivf_status ensure_capacity(ivf_ctx* c, int64_t e0) {
   if (e0 <= c->cap) return IVF_OK;
-  ST(alloc_means(c, e0 + c->nnz + 4096));
+  ST(alloc_means(c, e0 + e0 / 4 + 4096));  // later updates grow it on demand
   ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N, 1})));
   c->means_set = false;
   return IVF_OK;
@@ -943,11 +1026,13 @@ ivf_status ivf_load_objects(ivf_ctx* c, const int64_t* row_ptr, const int32_t* t
   CK(c, cudaMemcpyAsync(c->row_ptr, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, s));
   CK(c, cudaMemcpyAsync(c->term, term, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, s));
   CK(c, cudaMemcpyAsync(c->val32, val, sizeof(float) * c->nnz, cudaMemcpyDefault, s));
+  CK(c, cudaMemsetAsync(&c->dc->negative, 0, sizeof(unsigned), s));
   CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->val32,
                                c->cfg.storage == IVF_F32 ? nullptr : c->val_store, c->cfg.storage, c->nx, c->n_inst,
                                c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
-                               &c->dc->status, s));
+                               &c->dc->status, &c->dc->negative, s));
   if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
+  ST(read_objects_sign(c));
   c->members_valid = false;
   return IVF_OK;
 }
@@ -964,7 +1049,12 @@ ivf_status ivf_set_means(ivf_ctx* c, const int64_t* mean_ptr, const int32_t* mea
   std::vector<float> hv(e0);
   std::vector<double> hd(e0);
   CK(c, cudaMemcpy(hv.data(), mean_val, sizeof(float) * e0, cudaMemcpyDefault));
-  for (int64_t e = 0; e < e0; ++e) hd[e] = (double)hv[e];
+  bool nonneg = true;
+  for (int64_t e = 0; e < e0; ++e) {
+    hd[e] = (double)hv[e];
+    nonneg = nonneg && hv[e] >= 0.f;
+  }
+  c->means_nonneg = nonneg;
   CK(c, cudaMemcpyAsync(c->mptr[mb], hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(c->mterm[mb], mean_term, sizeof(int32_t) * e0, cudaMemcpyDefault, c->stream));
   CK(c, cudaMemcpyAsync(c->mval[mb], hd.data(), sizeof(double) * e0, cudaMemcpyHostToDevice, c->stream));
@@ -992,7 +1082,10 @@ ivf_status ivf_restore_means(ivf_ctx* c, const int64_t* ptr, const int32_t* term
   }
   CK(c, cudaMemcpyAsync(c->mptr[mb], hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(c->mterm[mb], ht.data(), sizeof(int32_t) * e0, cudaMemcpyHostToDevice, c->stream));
-  CK(c, cudaMemcpyAsync(c->mval[mb], val, sizeof(double) * e0, cudaMemcpyDefault, c->stream));
+  std::vector<double> hv(e0);
+  CK(c, cudaMemcpy(hv.data(), val, sizeof(double) * e0, cudaMemcpyDefault));
+  c->means_nonneg = std::all_of(hv.begin(), hv.end(), [](double x) { return x >= 0.0; });
+  CK(c, cudaMemcpyAsync(c->mval[mb], hv.data(), sizeof(double) * e0, cudaMemcpyHostToDevice, c->stream));
   CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 0,
                               c->stream));
   ST(finish_set_means(c));
@@ -1015,6 +1108,7 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
     }
     for (int32_t j = c->h_inst_clu[b]; j < c->h_inst_clu[b + 1]; ++j) ids[j] += (int32_t)c->h_inst_docs[b];
   }
+  c->means_nonneg = true;  // the means are objects, whose sign is known
   // row lengths on the host to size the means
   std::vector<int64_t> hrp(c->N + 1);
   CK(c, cudaMemcpy(hrp.data(), c->row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToHost));
@@ -1066,6 +1160,7 @@ ivf_status ivf_update(ivf_ctx* c) {
     CK(c, timing_event(c, &e1));
     c->tcalls.push_back({1, e0});
   }
+  ST(redo_update_if_overflow(c, c->alatest));
   c->mcur ^= 1;
   c->iteration += 1;
   c->members_valid = true;
@@ -1113,6 +1208,11 @@ ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_
       ST(enqueue_iteration(c, target, prev));
     }
     CK(c, cudaStreamSynchronize(c->stream));
+    if (c->hc->status & STS_CAPACITY) {
+      ST(redo_update_if_overflow(c, target));
+      CK(c, cudaMemcpyAsync(c->hc, c->dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    }
     c->alatest = target;
     c->mcur ^= 1;
     c->iteration += 1;

@@ -8,8 +8,10 @@ namespace ivfk {
 
 enum Storage : int { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
 
-// Candidate clusters kept per flagged object for the FP64 re-score.
-constexpr int CAND_MAX = 32;
+// Candidate clusters kept per flagged object for the FP64 re-score (more
+// candidates, or a flagged object beyond the slots of the candidate slab,
+// means a re-score against every cluster).
+constexpr int CAND_MAX = 128;
 
 // Device status word bits (ctx->d_status).
 enum StatusBits : unsigned {
@@ -46,7 +48,9 @@ struct AssignArgs {
   unsigned int* n_flagged;      // flagged objects (accumulated from 0)
   int32_t* flag_obj;            // [N]
   int32_t* flag_cnt;            // [N] candidates, -1 = overflow (all clusters)
-  int32_t* flag_cand;           // [N * CAND_MAX]
+  int32_t* flag_cand;           // [cand_slots * CAND_MAX]
+  int64_t cand_slots;           // flagged objects that get a candidate list
+  int32_t nonneg;               // all object values and mean values are >= 0
   // Dense head rows (the IFN form for the densest posting lists): term t with
   // head_slot[t] >= 0 is read from wd[head_slot[t] * kpad + cluster] instead
   // of its sparse list.  Used by the register-accumulator kernels (head_r > 0).
@@ -179,6 +183,8 @@ struct IvfBuildArgs {
   int64_t kpad;
   int64_t head_max;      // rows available in wd
   int64_t head_min_nc;   // a list of at least this many clusters is stored densely
+  float head_theta;      // ... or, with several instances, theta * K of the term's instance
+  const int64_t* inst_toff;  // [n_inst+1] term offsets of the instances
   uint32_t* hflags;      // [Dt+1] scratch
   int64_t* d_heads;      // [1] receives the number of dense rows
   // scratch
@@ -209,7 +215,7 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                    int32_t* term, const float* val32, void* val_store, int storage,
                                    float* nx, int32_t n_inst, const int64_t* inst_docs,
                                    const int64_t* inst_toff, const int32_t* inst_terms, int validate,
-                                   unsigned* status, cudaStream_t s);
+                                   unsigned* status, unsigned* negative, cudaStream_t s);
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
 

@@ -296,8 +296,16 @@ __global__ void k_toff(IvfBuildArgs a) {
 // paper's full inverted file (IFN) restricted to the densest lists.
 __global__ void k_head_flags(IvfBuildArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.dt; p += stride)
-    a.hflags[p] = (a.term_ptr[p + 1] - a.term_ptr[p] >= a.head_min_nc) ? 1u : 0u;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.dt; p += stride) {
+    int64_t min_nc = a.head_min_nc;
+    if (a.n_inst > 1) {  // theta * K of the term's own instance
+      const int b = find_inst64(a.inst_toff, a.n_inst, p);
+      const int64_t kb = a.inst_clu[b + 1] - a.inst_clu[b];
+      min_nc = (int64_t)ceilf(a.head_theta * (float)kb);
+      if (min_nc < 1) min_nc = 1;
+    }
+    a.hflags[p] = (a.term_ptr[p + 1] - a.term_ptr[p] >= min_nc) ? 1u : 0u;
+  }
 }
 
 __global__ void k_head_slots(IvfBuildArgs a) {
@@ -393,7 +401,7 @@ template <typename WT>
 __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_t* term, const float* val32,
                                   WT* val_store, float* nx, int32_t n_inst, const int64_t* inst_docs,
                                   const int64_t* inst_toff, const int32_t* inst_terms, int validate,
-                                  unsigned* status) {
+                                  unsigned* status, unsigned* negative) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -404,9 +412,11 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_
     const int64_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
     double ss = 0.0;
     bool bad = r1 < r0;
+    bool neg = false;
     for (int64_t h = r0 + lane; h < r1; h += 32) {
       const int32_t t = term[h];
       const float v = val32[h];
+      neg |= !(v >= 0.f);
       if (validate) {
         if (t < 0 || t >= d_local || !isfinite(v)) bad = true;
         if (h > r0 && term[h - 1] >= t) bad = true;
@@ -420,10 +430,12 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(IVF_FULL_MASK, ss, o);
     const bool any_bad = __any_sync(IVF_FULL_MASK, bad);
+    const bool any_neg = __any_sync(IVF_FULL_MASK, neg);
     if (lane == 0) {
       // an upper bound on ||x_i||: the FP64 sum is within a few ulps, then round up
       nx[i] = __double2float_ru(__dsqrt_ru(ss * (1.0 + 1e-12)));
       if (any_bad) atomicOr(status, (unsigned)STS_BAD_ROWS);
+      if (any_neg) atomicOr(negative, 1u);
     }
   }
 }
@@ -564,23 +576,26 @@ cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t
 cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local_max, const int64_t* row_ptr,
                                    int32_t* term, const float* val32, void* val_store, int storage, float* nx,
                                    int32_t n_inst, const int64_t* inst_docs, const int64_t* inst_toff,
-                                   const int32_t* inst_terms, int validate, unsigned* status, cudaStream_t s) {
+                                   const int32_t* inst_terms, int validate, unsigned* status, unsigned* negative,
+                                   cudaStream_t s) {
   (void)nnz;
   (void)dt_local_max;
   const unsigned g = grid_for(n_docs * 32, T256, 16384);
   switch (storage) {
     case ST_F16:
       k_prepare_objects<__half><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, static_cast<__half*>(val_store), nx,
-                                                   n_inst, inst_docs, inst_toff, inst_terms, validate, status);
+                                                   n_inst, inst_docs, inst_toff, inst_terms, validate, status,
+                                                   negative);
       break;
     case ST_BF16:
       k_prepare_objects<__nv_bfloat16><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32,
                                                           static_cast<__nv_bfloat16*>(val_store), nx, n_inst,
-                                                          inst_docs, inst_toff, inst_terms, validate, status);
+                                                          inst_docs, inst_toff, inst_terms, validate, status,
+                                                          negative);
       break;
     default:
       k_prepare_objects<float><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, nullptr, nx, n_inst, inst_docs,
-                                                  inst_toff, inst_terms, validate, status);
+                                                  inst_toff, inst_terms, validate, status, negative);
       break;
   }
   IVF_LAUNCH_CHECK();

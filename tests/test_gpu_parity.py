@@ -137,8 +137,9 @@ def test_batched_equals_single_instances():
         assert np.array_equal(mv[lo:hi], sv)
 
 
-def test_batched_lockstep_against_oracle():
-    ws = dg.batched_workloads(n_instances=4, n_range=(800, 2000), k_range=(8, 120), d_range=(2000, 5000),
+@pytest.mark.parametrize("kernel", ["sparse", "dense_head"])
+def test_batched_lockstep_against_oracle(kernel):
+    ws = dg.batched_workloads(n_instances=4, n_range=(800, 2000), k_range=(8, 1500), d_range=(2000, 5000),
                               nnz_range=(15.0, 50.0), iterations=3, seed=77)
     cs = [dg.make_corpus(w.corpus) for w in ws]
     ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
@@ -146,7 +147,7 @@ def test_batched_lockstep_against_oracle():
     offs = np.concatenate([[0], np.cumsum([c.nnz for c in cs])])
     row_ptr = np.concatenate([c.row_ptr[:-1] + o for c, o in zip(cs, offs)] + [[offs[-1]]]).astype(np.int64)
     with ivf.BatchedIVF(row_ptr, np.concatenate([c.term for c in cs]), np.concatenate([c.val for c in cs]),
-                        inst_docs, [c.n_terms for c in cs], [w.k for w in ws]) as m:
+                        inst_docs, [c.n_terms for c in cs], [w.k for w in ws], kernel=kernel) as m:
         m.set_means_from_docs(np.concatenate(ids))
         means = [sk.initial_means(c, d) for c, d in zip(cs, ids)]
         for r in range(3):
@@ -468,3 +469,25 @@ def test_dense_head_and_sparse_kernels_agree():
     assert np.array_equal(out["dense_head"][0], out["sparse"][0])
     assert np.allclose(out["dense_head"][1], out["sparse"][1], rtol=0, atol=1e-6)
     assert out["dense_head"][2] == out["sparse"][2]
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_means_capacity_grows_on_demand(use_graph):
+    """A context that starts with room for 1,000 mean entries grows while the
+    means fill up, and ends with the same result as a roomy context."""
+    c = corpus_for(3000, 4000, mean_len=30.0, seed=25)
+    k = 40
+    ids = dg.init_doc_ids(c.n_docs, k, 25)
+    out = []
+    for cap in (0, 1000):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, means_capacity=cap, use_graph=use_graph,
+                     kernel="sparse") as m:
+            m.set_means_from_docs(ids)
+            m.iterate(3)
+            m.assign(stats=False)
+            m.update()
+            out.append((m.get_assign(), m.get_means(), m.info()["ivf_capacity"]))
+    assert out[1][2] > 1000
+    assert np.array_equal(out[0][0], out[1][0])
+    for x, y in zip(out[0][1], out[1][1]):
+        assert np.array_equal(x, y)
