@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     p.add_argument("--n-docs", type=int, default=0, help="use only this many documents of the workload "
                    "(same generator; for small profiling cases)")
+    p.add_argument("--k", type=int, default=0, help="override the number of clusters (profiling cases)")
     p.add_argument("--kernel", choices=["auto", "dense_head", "sparse"], default="auto",
                    help="assignment kernel family (auto = the autotuner picks)")
     p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
@@ -188,12 +189,40 @@ def oracle_iteration_sample(corpus, means, assign_for_update, rng, budget_s: flo
     return t_assign + t_update, desc
 
 
+def paper_method_iteration_sample(corpus, means, assign_for_update, rng, budget_s: float, threads: int):
+    """Time Algorithm 3 in C (FP64, -O3; OpenMP over objects and clusters)
+    on the host cores: the assignment on a sample of objects scaled to all
+    of them, the update over all objects and clusters in full.
+    Returns (seconds per iteration, threads used, sample text)."""
+    import oracle.ivf_alg3 as calg3
+
+    xi = calg3.InvertedFile.from_means(means)
+    n = corpus.n_docs
+    nt = threads if threads > 0 else calg3.threads_available()
+    probe = rng.choice(n, size=min(n, 32 * nt), replace=False)
+    t = time.perf_counter()
+    calg3.assignment_step(corpus, xi, means.k, rows=probe, threads=nt)
+    per_obj = max((time.perf_counter() - t) / len(probe), 1e-8)
+    s = int(min(n, max(len(probe), 0.6 * budget_s / per_obj)))
+    rows = rng.choice(n, size=s, replace=False)
+    t = time.perf_counter()
+    calg3.assignment_step(corpus, xi, means.k, rows=rows, threads=nt)
+    t_assign = (time.perf_counter() - t) * n / s
+    t = time.perf_counter()
+    calg3.update_step(corpus, assign_for_update, means.k, prev=xi, threads=nt)
+    t_update = time.perf_counter() - t
+    desc = (f"Algorithm 3 in C on {nt} host thread(s): assignment of {s} random objects scaled x{n / s:.1f}, "
+            f"update in full ({t_update:.2f} s)")
+    return t_assign + t_update, nt, desc
+
+
 def workload(args):
     from paper_2002_09094_gb300 import datagen as dg
 
     w = dg.WORKLOADS[args.workload]
-    if args.n_docs:
-        w = w.scaled(n_docs=args.n_docs, name=f"{w.name}-first{args.n_docs}")
+    if args.n_docs or args.k:
+        name = w.name + (f"-first{args.n_docs}" if args.n_docs else "") + (f"-k{args.k}" if args.k else "")
+        w = w.scaled(n_docs=args.n_docs or None, k=args.k or None, name=name)
     return w
 
 
@@ -287,12 +316,18 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         barrier()
         t_begin = time.time()
+        torch.cuda.nvtx.range_push("timed")  # lets ncu --nvtx-include "timed/" pick the timed launches
+        step_ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
         ev0.record(stream)
-        for _ in range(args.steps):
+        step_ev[0].record(stream)
+        for s_i in range(args.steps):
             m.assign(stats=False)
             m.update()
+            step_ev[s_i + 1].record(stream)
         ev1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        step_ms = [step_ev[q].elapsed_time(step_ev[q + 1]) for q in range(args.steps)]
         barrier()
         t_end = time.time()
         total_ms = ev0.elapsed_time(ev1)
@@ -353,6 +388,8 @@ def run_ours(args, rank, world, local):
                       "kernel": ("dense_head r=%d theta=%.2f rows=%d" % (info["dense_head_r"], info["dense_head_theta"],
                                  info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
                       "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},
+           "step_ms": {"min": round(min(step_ms), 3), "median": round(statistics.median(step_ms), 3),
+                       "max": round(max(step_ms), 3)},
            "phases_ms_per_step": {"assign_kernel": round(kern_ms, 4),
                                   "assign_step": round(timing["assign_step_ms"] / n_steps, 4),
                                   "update": round(timing["update_ms"] / max(1, timing["n_update"]), 4)},
@@ -368,6 +405,14 @@ def run_ours(args, rank, world, local):
         v, desc = oracle_iteration_sample(c, means, assign_np, np.random.default_rng(1), args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": desc + "; means = the GPU's current FP64 means"}
+        # the paper's own method on the same host, one thread (as the paper
+        # runs it) and every core
+        pm = {}
+        for label, nt in (("one_thread", 1), ("all_threads", 0)):
+            v, used, desc = paper_method_iteration_sample(c, means, assign_np, np.random.default_rng(2),
+                                                          args.cpu_seconds / 2, nt)
+            pm[label] = {"value": v, "unit": UNIT, "cores": used, "sample": desc}
+        out["cpu_paper_method"] = {"kind": "Algorithm 3 (IVF) in C, FP64, gcc -O3", **pm}
     if rank == 0:
         emit(out)
     if dist is not None:
