@@ -74,9 +74,10 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(n_docs: int, storage: str):
+def traffic_per_launch(workload_name: str, storage: str):
     """DRAM bytes per assignment launch from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    when the kernel source changed since the counters were taken or the
+    counters are for another workload."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
@@ -84,6 +85,9 @@ def traffic_per_launch(n_docs: int, storage: str):
     sha = hashlib.sha256(open(ASSIGN_SRC, "rb").read()).hexdigest()
     m_sha = re.search(r"assign_cu_sha256:\s*([0-9a-f]+)", text)
     if not m_sha or m_sha.group(1) != sha:
+        return None
+    m_w = re.search(r"^workload:\s*(\S+)", text, re.M)
+    if not m_w or m_w.group(1) != workload_name:
         return None
     m = re.search(rf"bytes_per_launch\[{storage}\]:\s*([0-9.eE+]+)", text)
     return float(m.group(1)) if m else None
@@ -373,7 +377,7 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = peaks()
     achieved = b_assign / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(c.n_docs, args.storage),
+            "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(w.name, args.storage),
             "kernel": "k_assign", "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
             "kernel_ms": round(kern_ms, 4)}
@@ -385,8 +389,9 @@ def run_ours(args, rank, world, local):
                       "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (CSR %.2f GB); no flush" % (c.nnz * 8 / 1e9),
                       "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"],
-                      "kernel": ("dense_head r=%d theta=%.2f rows=%d" % (info["dense_head_r"], info["dense_head_theta"],
-                                 info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
+                      "kernel": ("dense_head r=%d sub=%d theta=%.2f rows=%d" % (
+                          info["dense_head_r"], info["dense_head_sub"], info["dense_head_theta"],
+                          info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
                       "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},
            "step_ms": {"min": round(min(step_ms), 3), "median": round(statistics.median(step_ms), 3),
                        "max": round(max(step_ms), 3)},
@@ -460,6 +465,13 @@ def run_batched(args, rank, world, local):
         launches = ivf.launch_count() - launches0
         a_batched = m.get_assign()
         info = m.info()
+        # phase split from one more (eager, event-timed) iteration, outside the timed region
+        m.timing_reset(True)
+        m.assign(stats=False)
+        m.update()
+        torch.cuda.synchronize()
+        tph = m.get_timing()
+        m.timing_reset(False)
         m.close()
         # the same instances, one context each, same iterations
         seq_ms = 0.0
@@ -485,6 +497,12 @@ def run_batched(args, rank, world, local):
                       "n_docs": int(inst_docs[-1]), "nnz": int(offs[-1]), "k_total": int(sum(w.k for w in ws)),
                       "storage": args.storage, "iterations": "graph-captured", "generation_s": round(gen_s, 1),
                       "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"]},
+           "phases_ms_one_eager_iteration": {"assign_kernel": round(tph["assign_kernel_ms"], 3),
+                                             "assign_step": round(tph["assign_step_ms"], 3),
+                                             "update": round(tph["update_ms"], 3)},
+           "kernel": ("dense_head r=%d sub=%d theta=%.2f" % (info["dense_head_r"], info["dense_head_sub"],
+                                                             info["dense_head_theta"]))
+           if info["dense_head_r"] else "sparse",
            "sequential_s_per_iter": seq_ms / 1e3, "batched_speedup": round(seq_ms / batched_ms, 3),
            "equal_assignments": equal, "converged": bool(conv), "gpu_launches": int(launches)}
     if rank == 0:

@@ -80,7 +80,10 @@ typedef struct {
                           assignments); 0: off */
   int32_t empty_policy;/* 0 keep previous mean (default), 1 empty mean */
   int32_t k_tile;      /* accumulator tile over the cluster range: 0 = autotune,
-                          else a power of two in [512, 65536] or >= k (no tiling) */
+                          else a power of two in [512, 65536] or >= k (no tiling);
+                          with IVF_FLAG_DENSE_HEAD it fixes the dense-head kernel's
+                          shared-memory tile (512: 512-cluster head tile; 1024 and
+                          more: k_tile / 1024 head tiles of 1,024 clusters) */
   int32_t warps_per_block; /* 0 = autotune, else 1..32 */
   uint32_t flags;      /* IVF_FLAG_* */
   int32_t means_capacity; /* entries reserved for the means / inverted file at create
@@ -111,7 +114,8 @@ typedef struct {
   int32_t iteration;       /* completed update steps */
   int32_t storage;
   int64_t device_bytes;    /* device memory held by the context */
-  int32_t dense_head_r;    /* 0: sparse kernel; else dense-head kernel with a 32*r-cluster tile */
+  int32_t dense_head_r;    /* 0: sparse kernel; else dense-head kernel with 32*r-cluster head tiles */
+  int32_t dense_head_sub;  /* head tiles per shared-memory tile of the dense-head kernel */
   float dense_head_theta;  /* lists covering >= theta * K clusters are stored densely */
   int64_t dense_head_rows; /* dense rows in the inverted file last built */
 } ivf_info;

@@ -19,15 +19,15 @@
 //     argmax.
 #include <float.h>
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
 namespace ivfk {
 
 namespace {
-
-constexpr int kMaxThreads = 1024;
-constexpr int kMaxThreadsHead = 32 * HEAD_MAX_WARPS;  // register accumulators need more than 64 registers
 
 __device__ __forceinline__ void top2_push(float& b, int& id, float& s, float x, int xid) {
   if (x > b || (x == b && xid < id)) {
@@ -190,8 +190,20 @@ __device__ __forceinline__ void unpack16<__nv_bfloat16>(uint4 raw, float* e) {
 // read-modify-writes; the remaining (sparse) lists scatter into the
 // shared-memory tile as in the R = 0 kernel.  Per cluster the head and the
 // tail contributions are each summed in ascending term order, then added.
-template <typename WT, typename IdT, int R>
-__global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assign(const AssignArgs a) {
+// SPLIT (R > 0 only): the shared-memory tile spans a.head_sub head sub-tiles;
+// the sparse lists are scattered once per tile, then each sub-tile walks the
+// dense rows.  Without SPLIT one pass per tile does both (head_sub == 1).
+//
+// Register budgets: 64 for the shared-memory kernel (1,024-thread blocks);
+// the dense-head kernels hold 32R-cluster accumulators and two rows in
+// flight -- 96 for FP32 rows, 128 for 16-bit rows of the 1,024-cluster tile
+// (no spills; 96 would spill there).
+template <typename WT, int R>
+constexpr int assign_max_regs() {
+  return R == 0 ? 64 : (sizeof(WT) == 4 ? 96 : (R >= 32 ? 128 : 96));
+}
+template <typename WT, typename IdT, int R, bool SPLIT = false>
+__global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArgs a) {
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* rho = smem + (size_t)warp * (a.tile_cap + 2 * CAND_MAX);
@@ -209,18 +221,20 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
   const int cmask = a.tiled ? (a.k_tile - 1) : 0xFFFF;
   const unsigned lt = (1u << lane) - 1u;
   unsigned long long my_entries = 0;
+  const bool nonneg = a.nonneg != 0 && (a.negative == nullptr || *a.negative == 0u) &&
+                      (a.means_negative == nullptr || *a.means_negative == 0u);
 
   for (;;) {
     unsigned long long o = 0;
     if (lane == 0) o = atomicAdd(a.work, 1ull);
     o = __shfl_sync(IVF_FULL_MASK, o, 0);
     if (o >= (unsigned long long)a.n_docs) break;
-    const int64_t i = (int64_t)o;
+    const int64_t i = (int64_t)o * a.obj_stride;
     const int b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
     const int K = a.inst_clu[b + 1] - a.inst_clu[b];
     const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
     const int m = (int)(r1 - r0);
-    const ErrBound bound = err_bound(m, a.nx[i], a.storage, a.nonneg != 0);
+    const ErrBound bound = err_bound(m, a.nx[i], a.storage, nonneg);
     const int tile = a.tiled ? a.k_tile : K;
     const int n_tiles = a.tiled ? (K + a.k_tile - 1) / a.k_tile : 1;
     float best = -INFINITY, second = -INFINITY;
@@ -229,71 +243,106 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
     bool overflow = false;
     const unsigned long long entries_before = my_entries;
 
-    for (int tt = 0; tt < n_tiles; ++tt) {
-      const int lo = tt * tile;
-      const int cnt = min(tile, K - lo);
-      // rho <- 0 over the tile
-      float4* r4 = reinterpret_cast<float4*>(rho);
-      for (int q = lane; q < ((cnt + 3) >> 2); q += 32) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int r = 0; r < RR; ++r) acc[r] = 0.f;
-      __syncwarp();
-      // for s in S_i (32 at a time): for (c, u) in xi_s: rho_c += v * u
-      for (int64_t h0 = r0; h0 < r1; h0 += 32) {
-        const int64_t h = h0 + lane;
-        int64_t beg = 0;
-        int len = 0;
-        int slot = -1;
-        float v = 0.f;
-        if (h < r1) {
-          const int t = __ldg(a.term + h);
-          v = to_f32(val[h]);
-          if (R > 0 && head_slot != nullptr) slot = __ldg(head_slot + t);
-          const int64_t tb = __ldg(a.term_ptr + t);
-          if (slot >= 0) {
-            // a dense row covers every tile: its list length counts once (Eq. 15)
-            if (tt == 0) len = (int)(__ldg(a.term_ptr + t + 1) - tb);
-          } else if (a.tiled) {
-            const int32_t* to = a.toff + (int64_t)t * (a.n_tiles_max + 1) + tt;
-            const int o0 = __ldg(to), o1 = __ldg(to + 1);
-            beg = tb + o0;
-            len = o1 - o0;
-          } else {
-            beg = tb;
-            len = (int)(__ldg(a.term_ptr + t + 1) - tb);
-          }
+    // One object term per lane: its value, dense-row slot (or -1), and the
+    // slice of its sparse list inside tile tt (count_head: the length of a
+    // dense row's list, counted once per object for Eq. 15).
+    struct TermInfo {
+      float v;
+      int slot;
+      int64_t beg;
+      int len;
+    };
+    auto load_term = [&](int64_t h, int tt, bool count_head) -> TermInfo {
+      float v = 0.f;
+      int slot = -1;
+      int64_t beg = 0;
+      int len = 0;
+      if (h < r1) {
+        const int t = __ldg(a.term + h);
+        v = to_f32(val[h]);
+        if (R > 0 && head_slot != nullptr) slot = __ldg(head_slot + t);
+        const int64_t tb0 = __ldg(a.term_ptr + t);
+        if (slot >= 0) {
+          if (count_head) len = (int)(__ldg(a.term_ptr + t + 1) - tb0);
+        } else if (a.tiled) {
+          const int32_t* to = a.toff + (int64_t)t * (a.n_tiles_max + 1) + tt;
+          const int o0 = __ldg(to), o1 = __ldg(to + 1);
+          beg = tb0 + o0;
+          len = o1 - o0;
+        } else {
+          beg = tb0;
+          len = (int)(__ldg(a.term_ptr + t + 1) - tb0);
         }
-        my_entries += (unsigned long long)len;
-        if constexpr (R > 0) {
-          // dense head rows of this chunk, two terms at a time (ascending term
-          // order per cluster): acc[g*VEC+k] += v * w[lo + VEC*(32g + lane) + k]
-          unsigned hm = __ballot_sync(IVF_FULL_MASK, slot >= 0);
-          while (hm) {
-            const int j0 = __ffs(hm) - 1;
-            hm &= hm - 1;
-            const bool two = hm != 0;
-            const int j1 = two ? __ffs(hm) - 1 : j0;
-            if (two) hm &= hm - 1;
-            const int s0 = __shfl_sync(IVF_FULL_MASK, slot, j0);
-            const int s1 = __shfl_sync(IVF_FULL_MASK, slot, j1);
-            const float v0 = __shfl_sync(IVF_FULL_MASK, v, j0);
-            const float v1 = two ? __shfl_sync(IVF_FULL_MASK, v, j1) : 0.f;  // fma(0, w, acc) == acc
-            const uint4* __restrict__ row0 = reinterpret_cast<const uint4*>(wd + (int64_t)s0 * a.kpad + lo) + lane;
-            const uint4* __restrict__ row1 = reinterpret_cast<const uint4*>(wd + (int64_t)s1 * a.kpad + lo) + lane;
-            uint4 w0[NG], w1[NG];
+      }
+      return TermInfo{v, slot, beg, len};
+    };
+    // The sparse lists of one chunk, one at a time: rho_c += v * u.
+    auto tail_scatter = [&](unsigned tm, int64_t beg, int len, float v) {
+      while (tm) {
+        const int j = __ffs(tm) - 1;
+        tm &= tm - 1;
+        const int64_t bj = __shfl_sync(IVF_FULL_MASK, beg, j);
+        const int lj = __shfl_sync(IVF_FULL_MASK, len, j);
+        const float vj = __shfl_sync(IVF_FULL_MASK, v, j);
+        const IdT* __restrict__ cp = cid + bj;
+        const WT* __restrict__ wp = w + bj;
+        int q = lane;
+        for (; q + 96 < lj; q += 128) {
+          const int c0 = __ldg(cp + q) & cmask;
+          const int c1 = __ldg(cp + q + 32) & cmask;
+          const int c2 = __ldg(cp + q + 64) & cmask;
+          const int c3 = __ldg(cp + q + 96) & cmask;
+          const float u0 = to_f32(wp[q]);
+          const float u1 = to_f32(wp[q + 32]);
+          const float u2 = to_f32(wp[q + 64]);
+          const float u3 = to_f32(wp[q + 96]);
+          rho[c0] = fmaf(vj, u0, rho[c0]);
+          rho[c1] = fmaf(vj, u1, rho[c1]);
+          rho[c2] = fmaf(vj, u2, rho[c2]);
+          rho[c3] = fmaf(vj, u3, rho[c3]);
+        }
+        for (; q < lj; q += 32) {
+          const int c = __ldg(cp + q) & cmask;
+          rho[c] = fmaf(vj, to_f32(wp[q]), rho[c]);
+        }
+        __syncwarp();
+      }
+    };
+    // The dense head rows of one chunk, two at a time (ascending term order
+    // per cluster): acc[g*VEC+k] += v * w[slo + VEC*(32g + lane) + k].
+    auto head_rows = [&](unsigned hm, int slot, float v, int slo, int ng_live) {
+      if constexpr (R > 0) {
+        while (hm) {
+          const int j0 = __ffs(hm) - 1;
+          hm &= hm - 1;
+          const bool two = hm != 0;
+          const int j1 = two ? __ffs(hm) - 1 : j0;
+          if (two) hm &= hm - 1;
+          const int s0 = __shfl_sync(IVF_FULL_MASK, slot, j0);
+          const int s1 = __shfl_sync(IVF_FULL_MASK, slot, j1);
+          const float v0 = __shfl_sync(IVF_FULL_MASK, v, j0);
+          const float v1 = two ? __shfl_sync(IVF_FULL_MASK, v, j1) : 0.f;  // fma(0, w, acc) == acc
+          const uint4* __restrict__ row0 = reinterpret_cast<const uint4*>(wd + (int64_t)s0 * a.kpad + slo) + lane;
+          const uint4* __restrict__ row1 = reinterpret_cast<const uint4*>(wd + (int64_t)s1 * a.kpad + slo) + lane;
+          // groups that lie wholly past the sub-tile's last cluster are
+          // skipped (warp-uniform), so a small K does not pay for the full width
+          uint4 w0[NG], w1[NG];
 #pragma unroll
-            for (int g = 0; g < NG; ++g) w0[g] = __ldg(row0 + 32 * g);
+          for (int g = 0; g < NG; ++g) w0[g] = __ldg(row0 + 32 * g);
 #pragma unroll
-            for (int g = 0; g < NG; ++g) w1[g] = __ldg(row1 + 32 * g);
+          for (int g = 0; g < NG; ++g) w1[g] = __ldg(row1 + 32 * g);
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
+          for (int g = 0; g < NG; ++g) {
+            if (g < ng_live) {
               float e[VEC];
               unpack16<WT>(w0[g], e);
 #pragma unroll
               for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = fmaf(v0, e[k], acc[g * VEC + k]);
             }
+          }
 #pragma unroll
-            for (int g = 0; g < NG; ++g) {
+          for (int g = 0; g < NG; ++g) {
+            if (g < ng_live) {
               float e[VEC];
               unpack16<WT>(w1[g], e);
 #pragma unroll
@@ -301,63 +350,74 @@ __global__ void __launch_bounds__(R > 0 ? kMaxThreadsHead : kMaxThreads) k_assig
             }
           }
         }
-        // sparse lists of this chunk, one at a time
-        unsigned tm = __ballot_sync(IVF_FULL_MASK, h < r1 && slot < 0);
-        while (tm) {
-          const int j = __ffs(tm) - 1;
-          tm &= tm - 1;
-          const int64_t bj = __shfl_sync(IVF_FULL_MASK, beg, j);
-          const int lj = __shfl_sync(IVF_FULL_MASK, len, j);
-          const float vj = __shfl_sync(IVF_FULL_MASK, v, j);
-          const IdT* __restrict__ cp = cid + bj;
-          const WT* __restrict__ wp = w + bj;
-          int q = lane;
-          for (; q + 96 < lj; q += 128) {
-            const int c0 = __ldg(cp + q) & cmask;
-            const int c1 = __ldg(cp + q + 32) & cmask;
-            const int c2 = __ldg(cp + q + 64) & cmask;
-            const int c3 = __ldg(cp + q + 96) & cmask;
-            const float u0 = to_f32(wp[q]);
-            const float u1 = to_f32(wp[q + 32]);
-            const float u2 = to_f32(wp[q + 64]);
-            const float u3 = to_f32(wp[q + 96]);
-            rho[c0] = fmaf(vj, u0, rho[c0]);
-            rho[c1] = fmaf(vj, u1, rho[c1]);
-            rho[c2] = fmaf(vj, u2, rho[c2]);
-            rho[c3] = fmaf(vj, u3, rho[c3]);
-          }
-          for (; q < lj; q += 32) {
-            const int c = __ldg(cp + q) & cmask;
-            rho[c] = fmaf(vj, to_f32(wp[q]), rho[c]);
-          }
-          __syncwarp();
+      }
+    };
+
+    // R > 0: the shared-memory tile holds head_sub head sub-tiles of 32R
+    // clusters.  With one sub-tile the chunk loop does both kinds of list in
+    // one pass; with several (SPLIT), the sparse lists are scattered once per
+    // tile and each sub-tile then walks the object's dense rows into registers.
+    constexpr bool split = R > 0 && SPLIT;
+    for (int tt = 0; tt < n_tiles; ++tt) {
+      const int lo = tt * tile;
+      const int cnt = min(tile, K - lo);
+      // rho <- 0 over the tile
+      float4* r4 = reinterpret_cast<float4*>(rho);
+      for (int q = lane; q < ((cnt + 3) >> 2); q += 32) r4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncwarp();
+      // for s in S_i (32 at a time): for (c, u) in xi_s: rho_c += v * u
+      if constexpr (R == 0 || split) {
+        for (int64_t h0 = r0; h0 < r1; h0 += 32) {
+          const TermInfo ti0 = load_term(h0 + lane, tt, tt == 0);
+          my_entries += (unsigned long long)ti0.len;
+          tail_scatter(__ballot_sync(IVF_FULL_MASK, h0 + lane < r1 && ti0.slot < 0), ti0.beg, ti0.len, ti0.v);
         }
       }
       // argmax over the tile: lowest id among the maxima, plus the runner-up
       float tb = -INFINITY, ts = -INFINITY;
       int ti = 0x7fffffff;
       if constexpr (R > 0) {  // rho_c = head part (registers) + tail part (shared memory)
+        constexpr int SUB = 32 * RR;
+        const int nsub = split ? (cnt + SUB - 1) / SUB : 1;
+        for (int sb = 0; sb < nsub; ++sb) {
+          const int sbase = sb * SUB;
+          const int scnt = min(SUB, cnt - sbase);
+          const int ng_live = (scnt + VEC * 32 - 1) / (VEC * 32);  // 16-byte groups holding a cluster < scnt
 #pragma unroll
-        for (int g = 0; g < NG; ++g) {
+          for (int r = 0; r < RR; ++r) acc[r] = 0.f;
+          for (int64_t h0 = r0; h0 < r1; h0 += 32) {
+            const TermInfo ti0 = load_term(h0 + lane, tt, !split && tt == 0);
+            if (!split) my_entries += (unsigned long long)ti0.len;
+            head_rows(__ballot_sync(IVF_FULL_MASK, ti0.slot >= 0), ti0.slot, ti0.v, lo + sbase, ng_live);
+            if (!split)
+              tail_scatter(__ballot_sync(IVF_FULL_MASK, h0 + lane < r1 && ti0.slot < 0), ti0.beg, ti0.len, ti0.v);
+          }
+          __syncwarp();
+          float* rs = rho + sbase;
 #pragma unroll
-          for (int k4 = 0; k4 < VEC; k4 += 4) {
-            const int q0 = VEC * 32 * g + VEC * lane + k4;  // 16-byte aligned, < tile_cap
-            float4 t4 = *reinterpret_cast<const float4*>(rho + q0);
-            float x[4] = {acc[g * VEC + k4] + t4.x, acc[g * VEC + k4 + 1] + t4.y, acc[g * VEC + k4 + 2] + t4.z,
-                          acc[g * VEC + k4 + 3] + t4.w};
-            if (q0 + 3 < cnt) {
-              *reinterpret_cast<float4*>(rho + q0) = make_float4(x[0], x[1], x[2], x[3]);
+          for (int g = 0; g < NG; ++g) {
+            if (g >= ng_live) continue;
 #pragma unroll
-              for (int k = 0; k < 4; ++k) top2_push(tb, ti, ts, x[k], lo + q0 + k);
-            } else {
+            for (int k4 = 0; k4 < VEC; k4 += 4) {
+              const int q0 = VEC * 32 * g + VEC * lane + k4;  // 16-byte aligned, < SUB
+              float4 t4 = *reinterpret_cast<const float4*>(rs + q0);
+              float x[4] = {acc[g * VEC + k4] + t4.x, acc[g * VEC + k4 + 1] + t4.y, acc[g * VEC + k4 + 2] + t4.z,
+                            acc[g * VEC + k4 + 3] + t4.w};
+              if (q0 + 3 < scnt) {
+                *reinterpret_cast<float4*>(rs + q0) = make_float4(x[0], x[1], x[2], x[3]);
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                if (q0 + k < cnt) {
-                  rho[q0 + k] = x[k];
-                  top2_push(tb, ti, ts, x[k], lo + q0 + k);
-                }
+                for (int k = 0; k < 4; ++k) top2_push(tb, ti, ts, x[k], lo + sbase + q0 + k);
+              } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  if (q0 + k < scnt) {
+                    rs[q0 + k] = x[k];
+                    top2_push(tb, ti, ts, x[k], lo + sbase + q0 + k);
+                  }
+              }
             }
           }
+          __syncwarp();
         }
       } else {
         for (int q = lane; q < cnt; q += 32) top2_push(tb, ti, ts, rho[q], lo + q);
@@ -569,10 +629,15 @@ __global__ void k_reduce_final(const ReduceArgs a, int nblocks) {
 }
 
 template <typename WT>
-const void* assign_fn_r(int head_r) {
+const void* assign_fn_r(int head_r, int head_sub) {
+  if (head_sub > 1)
+    return head_r == HEAD_R_LARGE ? reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE, true>)
+                                  : nullptr;
   switch (head_r) {
     case HEAD_R_SMALL:
       return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_SMALL>);
+    case HEAD_R_MID:
+      return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_MID>);
     case HEAD_R_LARGE:
       return reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE>);
     default:
@@ -580,22 +645,29 @@ const void* assign_fn_r(int head_r) {
   }
 }
 
-const void* assign_fn_for(int storage, int head_r) {
+const void* assign_fn_for(int storage, int head_r, int head_sub) {
   switch (storage) {
     case ST_F16:
-      return assign_fn_r<__half>(head_r);
+      return assign_fn_r<__half>(head_r, head_sub);
     case ST_BF16:
-      return assign_fn_r<__nv_bfloat16>(head_r);
+      return assign_fn_r<__nv_bfloat16>(head_r, head_sub);
     default:
-      return assign_fn_r<float>(head_r);
+      return assign_fn_r<float>(head_r, head_sub);
   }
 }
 
 template <typename WT>
 void launch_typed(const AssignArgs& a, int warps, int blocks, size_t smem, cudaStream_t s, int head_r) {
+  if (head_r == HEAD_R_LARGE && a.head_sub > 1) {
+    k_assign<WT, uint16_t, HEAD_R_LARGE, true><<<blocks, warps * 32, smem, s>>>(a);
+    return;
+  }
   switch (head_r) {
     case HEAD_R_SMALL:
       k_assign<WT, uint16_t, HEAD_R_SMALL><<<blocks, warps * 32, smem, s>>>(a);
+      break;
+    case HEAD_R_MID:
+      k_assign<WT, uint16_t, HEAD_R_MID><<<blocks, warps * 32, smem, s>>>(a);
       break;
     case HEAD_R_LARGE:
       k_assign<WT, uint16_t, HEAD_R_LARGE><<<blocks, warps * 32, smem, s>>>(a);
@@ -612,22 +684,35 @@ size_t assign_smem_bytes(int tile_cap, int warps) {
   return (size_t)warps * ((size_t)tile_cap + 2 * CAND_MAX) * sizeof(float);
 }
 
-cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r) {
+// The shared-memory opt-in of a kernel is process-wide, so it only ever grows:
+// a context with a smaller tile must not lower it under another's launches.
+cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r, int head_sub) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> raised;
   const size_t bytes = assign_smem_bytes(tile_cap, warps);
-  return cudaFuncSetAttribute(assign_fn_for(storage, head_r), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bytes);
+  const void* fn = assign_fn_for(storage, head_r, head_sub);
+  if (fn == nullptr) return cudaErrorInvalidValue;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = raised[fn];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
-int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r) {
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r, int head_sub) {
   int nb = 0;
-  if (assign_prepare(storage, tile_cap, warps, head_r) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage, head_r), warps * 32,
+  if (assign_prepare(storage, tile_cap, warps, head_r, head_sub) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage, head_r, head_sub), warps * 32,
                                                     assign_smem_bytes(tile_cap, warps)) != cudaSuccess)
     return 0;
   return nb;
 }
 
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r) {
+  if ((a.tiled && a.toff == nullptr) || (head_r > 0 && (a.head_slot == nullptr || a.wd == nullptr)) ||
+      a.head_sub < 1 || (a.head_sub > 1 && head_r != HEAD_R_LARGE))
+    return cudaErrorInvalidValue;
   const size_t smem = assign_smem_bytes(a.tile_cap, warps);
   switch (a.storage) {
     case ST_F16:

@@ -41,6 +41,7 @@ struct DevCounters {
   unsigned long long acc_rescored;
   long long heads;                  // dense head rows of the inverted file last built
   unsigned int negative;            // some object value is negative (not an error)
+  unsigned int means_negative[2];   // some value of means buffer 0 / 1 is negative
 };
 
 struct Shape {
@@ -50,6 +51,7 @@ struct Shape {
   int warps = 0;
   int blocks = 0;
   int head_r = 0;     // registers per lane of the dense-head accumulator (0 = no dense head)
+  int head_sub = 1;   // dense-head sub-tiles (32 * head_r clusters) per shared-memory tile
   float head_theta = 0.f;  // a list covering at least this fraction of K is stored densely
 };
 
@@ -154,8 +156,6 @@ struct ivf_ctx {
   bool tuned_on_updated_means = false;  // the choice was made on means from an update step
   // state
   bool means_set = false;
-  bool objects_nonneg = true;  // every object value >= 0
-  bool means_nonneg = true;    // every mean value >= 0
   int64_t cand_slots = 0;      // flagged objects with room for a candidate list
   int32_t iteration = 0;
   // graphs keyed by (mcur, alatest)
@@ -300,16 +300,6 @@ ivf_status check_status(ivf_ctx* c) {
   return IVF_OK;
 }
 
-// Whether every object value is >= 0 (then every mean built from objects is
-// too, and the assignment uses the similarity-relative error bound).
-ivf_status read_objects_sign(ivf_ctx* c) {
-  unsigned neg = 0;
-  CK(c, cudaMemcpyAsync(&neg, &c->dc->negative, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
-  CK(c, cudaStreamSynchronize(c->stream));
-  c->objects_nonneg = neg == 0;
-  return IVF_OK;
-}
-
 // --------------------------------------------------------------- create
 
 ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vector<int64_t>& inst_docs,
@@ -331,6 +321,10 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
     cudaError_t es = cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault);
     if (es != cudaSuccess) return bail(fail_cuda(c, "cudaStreamCreate", es));
     c->own_stream = true;
+  }
+  {
+    cudaError_t er = radix_prepare();
+    if (er != cudaSuccess) return bail(fail_cuda(c, "radix_prepare", er));
   }
   // instance tables
   c->h_inst_docs = inst_docs;
@@ -418,10 +412,6 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->d_nnz, 1);
   AL(c->d_n, 1);
   AL(c->d_u, 1);
-  // smallest tile gives the longest per-term offset rows
-  const int64_t tiles_max = ceil_div(c->kmax, kTileChoices[0]);
-  c->toff_len = c->Dt * (tiles_max + 1);
-  if (c->kmax > kTileChoices[0]) AL(c->toff, c->toff_len);
 #undef AL
   e = cudaMallocHost(&c->hc, sizeof(DevCounters));
   if (e != cudaSuccess) return bail(fail_cuda(c, "cudaMallocHost", e));
@@ -435,7 +425,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
                        : nnz > (int64_t(400) << 20) ? nnz / 2 + 4096
                                                      : nnz + nnz / 4 + 4096;
   if ((s = alloc_means(c, cap0)) != IVF_OK) return bail(s);
-  if ((s = alloc_scratch(c, std::max<int64_t>({nnz, c->cap, N, 1}))) != IVF_OK) return bail(s);
+  if ((s = alloc_scratch(c, std::max<int64_t>({nnz, c->cap, N + 1}))) != IVF_OK) return bail(s);
 
   cudaStream_t st = c->stream;
 #define CKB(expr)                                   \
@@ -460,7 +450,6 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
                              &c->dc->status, &c->dc->negative, st));
 #undef CKB
   if ((s = check_status(c)) != IVF_OK) return bail(s);
-  if ((s = read_objects_sign(c)) != IVF_OK) return bail(s);
   *out = c;
   return IVF_OK;
 }
@@ -580,21 +569,32 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
   a.flag_cnt = c->flag_cnt;
   a.flag_cand = c->flag_cand;
   a.cand_slots = c->cand_slots;
-  a.nonneg = (c->objects_nonneg && c->means_nonneg) ? 1 : 0;
+  // the kernel reads the sign flags of the objects and of the means buffer
+  // the inverted file was built from, so no host copy of them is needed
+  a.nonneg = 1;
+  a.negative = &c->dc->negative;
+  a.means_negative = &c->dc->means_negative[c->mcur];
   if (sh.head_r > 0) {
     a.head_slot = c->head_slot;
     a.wd = c->wd;
     a.kpad = c->kpad;
+    a.head_sub = sh.head_sub;
   }
   return a;
 }
 
-// head_r > 0 selects the dense-head kernel, whose tile is 32 * head_r clusters.
-bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f) {
+// head_r > 0 selects the dense-head kernel, whose shared-memory tile is
+// head_sub sub-tiles of 32 * head_r clusters.
+bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f,
+               int head_sub = 1) {
   Shape sh;
-  if (head_r > 0) k_tile = 32 * head_r;
+  if (head_r > 0) {
+    if (head_sub < 1 || !is_pow2(head_sub)) return false;
+    k_tile = 32 * head_r * head_sub;
+  }
   if (k_tile <= 0 || k_tile >= c->kmax) {
     if (c->kmax > 65536) return false;
+    if (head_r > 0 && head_sub > 1 && 32 * head_r * (head_sub / 2) >= c->kmax) return false;  // no gain
     sh.tiled = 0;
     sh.k_tile = c->kmax;
     sh.tile_cap = (c->kmax + 3) & ~3;
@@ -604,9 +604,10 @@ bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0
     sh.k_tile = k_tile;
     sh.tile_cap = k_tile;
   }
-  // the dense-head kernel reads whole 16-byte groups of the 32R-cluster tile
-  if (head_r > 0) sh.tile_cap = 32 * head_r;
+  // the dense-head kernel reads whole 16-byte groups of each 32R-cluster sub-tile
+  if (head_r > 0) sh.tile_cap = (int)ceil_div((int64_t)sh.k_tile, 32 * head_r) * 32 * head_r;
   sh.head_r = head_r;
+  sh.head_sub = head_r > 0 ? head_sub : 1;
   sh.head_theta = theta;
   const size_t per_warp = ((size_t)sh.tile_cap + 2 * CAND_MAX) * sizeof(float);
   int wmax = (int)std::min<size_t>(kSmemBudget / per_warp, head_r > 0 ? HEAD_MAX_WARPS : 16);
@@ -615,16 +616,31 @@ bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0
   int warps = warps_req > 0 ? std::min(warps_req, wmax) : std::min(wmax, 8);
   if (warps_req > 0 && (size_t)warps_req * per_warp > kSmemBudget) return false;
   sh.warps = warps;
-  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps, head_r);
+  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps, head_r, sh.head_sub);
   if (bps < 1) return false;
   sh.blocks = bps * c->num_sms;
   *out = sh;
   return true;
 }
 
+// Per-(term, tile) offsets for tiles of k_tile clusters: the smallest tile
+// in use gives the longest rows, so the buffer only ever grows.
+ivf_status ensure_toff(ivf_ctx* c, int k_tile) {
+  const int64_t need = c->Dt * (ceil_div(c->kmax, k_tile) + 1);
+  if (c->toff && c->toff_len >= need) return IVF_OK;
+  dfree(c, c->toff);
+  c->toff = nullptr;
+  c->toff_len = 0;
+  ST(dalloc(c, &c->toff, need));
+  c->toff_len = need;
+  drop_graphs(c);
+  return IVF_OK;
+}
+
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
+  if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
   c->shape = sh;
-  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r));
+  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r, sh.head_sub));
   if (sh.head_r > 0) ST(alloc_head(c, sh.head_r));
   IvfBuildArgs a = ivf_args(c, c->mcur);
   if (sh.tiled) CK(c, launch_build_toff(a, c->stream));
@@ -643,8 +659,15 @@ ivf_status autotune(ivf_ctx* c) {
   std::vector<Shape> cands;
   Shape sh;
   if (c->cfg.k_tile > 0) {
-    if (!shape_for(c, c->cfg.k_tile, c->cfg.warps_per_block, &sh))
-      return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
+    bool ok;
+    if (c->cfg.flags & IVF_FLAG_DENSE_HEAD) {
+      const int hr = c->cfg.k_tile < 32 * HEAD_R_LARGE ? HEAD_R_MID : HEAD_R_LARGE;
+      ok = c->cfg.k_tile % (32 * hr) == 0 &&
+           shape_for(c, 0, c->cfg.warps_per_block, &sh, hr, 0.25f, c->cfg.k_tile / (32 * hr));
+    } else {
+      ok = shape_for(c, c->cfg.k_tile, c->cfg.warps_per_block, &sh);
+    }
+    if (!ok) return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
     cands.push_back(sh);
   } else {
     const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0;
@@ -655,10 +678,30 @@ ivf_status autotune(ivf_ctx* c) {
         if (t < c->kmax && shape_for(c, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
     }
     // dense-head kernels (the IFN form for lists covering >= theta K clusters)
-    const int hr = c->kmax <= 32 * HEAD_R_SMALL ? HEAD_R_SMALL : HEAD_R_LARGE;
-    if (!no_head)
-      for (float theta : {0.5f, 0.25f})
-        if (shape_for(c, 0, c->cfg.warps_per_block, &sh, hr, theta)) cands.push_back(sh);
+    // 512- and 1,024-cluster tiles (fewer registers and more warps per SM
+    // against fewer passes over the object's terms); 4-warp blocks fit more
+    // warps per SM than 8-warp blocks at ~96 registers
+    std::vector<int> rs;
+    if (c->kmax <= 32 * HEAD_R_SMALL)
+      rs = {HEAD_R_SMALL};
+    else
+      rs = {HEAD_R_MID, HEAD_R_LARGE};
+    if (!no_head) {
+      for (int hr : rs)
+        for (float theta : {0.5f, 0.25f})
+          for (int wp : {8, 4}) {
+            if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
+            if (hr != HEAD_R_LARGE && wp != 8) continue;
+            if (shape_for(c, 0, wp, &sh, hr, theta)) cands.push_back(sh);
+          }
+      // wider shared-memory tiles for the sparse lists (fewer, longer
+      // per-tile slices when K spans many head sub-tiles)
+      for (int sub : {2, 4})
+        for (int wp : {4, 8}) {
+          if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
+          if (shape_for(c, 0, wp, &sh, HEAD_R_LARGE, 0.25f, sub)) cands.push_back(sh);
+        }
+    }
   }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
   // Contexts of the same shape in one process reuse the first choice, so
@@ -690,6 +733,11 @@ ivf_status autotune(ivf_ctx* c) {
   for (const Shape& cand : cands) {
     ST(set_shape(c, cand));
     AssignArgs a = assign_args(c, cand, target, 0);
+    // Large problems are timed on every s-th object (s <= 16, at least 65,536
+    // objects): a sample that spans every instance of a batched context.
+    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(16, c->N >> 16));
+    a.obj_stride = (int32_t)stride;
+    a.n_docs = (c->N + stride - 1) / stride;
     float ms_min = 1e30f;
     for (int rep = 0; rep < 2; ++rep) {
       CK(c, cudaMemsetAsync(c->dc, 0, sizeof(unsigned long long) * 2, c->stream));
@@ -830,6 +878,8 @@ ivf_status enqueue_update(ivf_ctx* c, int src) {
   u.d_u = c->d_u;
   u.temp = c->temp;
   u.status = &c->dc->status;
+  u.means_negative = &c->dc->means_negative[mn];
+  CK(c, cudaMemsetAsync(u.means_negative, 0, sizeof(unsigned), c->stream));
   CK(c, launch_update_means(u, c->stream));
   ST(enqueue_build_ivf(c, mn));
   return IVF_OK;
@@ -896,8 +946,8 @@ ivf_status grow_means(ivf_ctx* c, int64_t new_cap) {
   ST(dalloc(c, &wp, (new_cap + 8) * (int64_t)storage_bytes(c->cfg.storage)));
   c->w = wp;
   c->cap = new_cap;
-  if (std::max<int64_t>({c->nnz, c->cap, c->N, 1}) > c->scratch_len)
-    ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N, 1})));
+  if (std::max<int64_t>({c->nnz, c->cap, c->N + 1}) > c->scratch_len)
+    ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N + 1})));
   drop_graphs(c);
   return IVF_OK;
 }
@@ -923,7 +973,7 @@ ivf_status redo_update_if_overflow(ivf_ctx* c, int src) {
 ivf_status ensure_capacity(ivf_ctx* c, int64_t e0) {
   if (e0 <= c->cap) return IVF_OK;
   ST(alloc_means(c, e0 + e0 / 4 + 4096));  // later updates grow it on demand
-  ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N, 1})));
+  ST(alloc_scratch(c, std::max<int64_t>({c->nnz, c->cap, c->N + 1})));
   c->means_set = false;
   return IVF_OK;
 }
@@ -937,6 +987,11 @@ ivf_status finish_set_means(ivf_ctx* c) {
   c->means_set = true;
   c->alatest = -1;
   c->iteration = 0;
+  // new means: the kernel is chosen again (a cached choice for this shape
+  // is taken as is), so a context follows the same kernel sequence as a
+  // fresh one given the same data
+  c->tuned = false;
+  c->tuned_on_updated_means = false;
   c->members_valid = false;
   drop_graphs(c);
   return IVF_OK;
@@ -1017,13 +1072,22 @@ ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* ins
 
 ivf_status ivf_load_objects(ivf_ctx* c, const int64_t* row_ptr, const int32_t* term, const float* val) {
   if (!c || !row_ptr || (c->nnz > 0 && (!term || !val))) return fail(c, IVF_E_INVALID, "null argument");
-  std::vector<int64_t> hrp(c->N + 1);
-  CK(c, cudaMemcpy(hrp.data(), row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault));
-  if (hrp[0] != 0 || hrp[c->N] != c->nnz) return fail(c, IVF_E_INVALID, "row_ptr must start at 0 and end at nnz");
-  for (int64_t i = 0; i < c->N; ++i)
-    if (hrp[i + 1] < hrp[i]) return fail(c, IVF_E_INVALID, "row_ptr must be non-decreasing");
   cudaStream_t s = c->stream;
-  CK(c, cudaMemcpyAsync(c->row_ptr, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, s));
+  // row_ptr is checked on the device, in scratch, before the context's copy
+  // changes: the one synchronisation of this call.
+  int64_t* rp_new = reinterpret_cast<int64_t*>(c->k64a);  // scratch_len >= N + 1
+  CK(c, cudaMemcpyAsync(rp_new, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, s));
+  CK(c, launch_check_row_ptr(rp_new, c->N, c->nnz, &c->dc->status, s));
+  {
+    unsigned st = 0;
+    CK(c, cudaMemcpyAsync(&st, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    CK(c, cudaStreamSynchronize(s));
+    if (st & STS_BAD_ROWS) {
+      CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), s));
+      return fail(c, IVF_E_INVALID, "row_ptr must start at 0, end at nnz and be non-decreasing");
+    }
+  }
+  CK(c, cudaMemcpyAsync(c->row_ptr, rp_new, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToDevice, s));
   CK(c, cudaMemcpyAsync(c->term, term, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, s));
   CK(c, cudaMemcpyAsync(c->val32, val, sizeof(float) * c->nnz, cudaMemcpyDefault, s));
   CK(c, cudaMemsetAsync(&c->dc->negative, 0, sizeof(unsigned), s));
@@ -1032,7 +1096,6 @@ ivf_status ivf_load_objects(ivf_ctx* c, const int64_t* row_ptr, const int32_t* t
                                c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
                                &c->dc->status, &c->dc->negative, s));
   if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
-  ST(read_objects_sign(c));
   c->members_valid = false;
   return IVF_OK;
 }
@@ -1049,17 +1112,13 @@ ivf_status ivf_set_means(ivf_ctx* c, const int64_t* mean_ptr, const int32_t* mea
   std::vector<float> hv(e0);
   std::vector<double> hd(e0);
   CK(c, cudaMemcpy(hv.data(), mean_val, sizeof(float) * e0, cudaMemcpyDefault));
-  bool nonneg = true;
-  for (int64_t e = 0; e < e0; ++e) {
-    hd[e] = (double)hv[e];
-    nonneg = nonneg && hv[e] >= 0.f;
-  }
-  c->means_nonneg = nonneg;
+  for (int64_t e = 0; e < e0; ++e) hd[e] = (double)hv[e];
   CK(c, cudaMemcpyAsync(c->mptr[mb], hp.data(), sizeof(int64_t) * (c->Kt + 1), cudaMemcpyHostToDevice, c->stream));
   CK(c, cudaMemcpyAsync(c->mterm[mb], mean_term, sizeof(int32_t) * e0, cudaMemcpyDefault, c->stream));
   CK(c, cudaMemcpyAsync(c->mval[mb], hd.data(), sizeof(double) * e0, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemsetAsync(&c->dc->means_negative[mb], 0, sizeof(unsigned), c->stream));
   CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 1,
-                              c->stream));
+                              &c->dc->means_negative[mb], c->stream));
   return finish_set_means(c);
 }
 
@@ -1084,10 +1143,10 @@ ivf_status ivf_restore_means(ivf_ctx* c, const int64_t* ptr, const int32_t* term
   CK(c, cudaMemcpyAsync(c->mterm[mb], ht.data(), sizeof(int32_t) * e0, cudaMemcpyHostToDevice, c->stream));
   std::vector<double> hv(e0);
   CK(c, cudaMemcpy(hv.data(), val, sizeof(double) * e0, cudaMemcpyDefault));
-  c->means_nonneg = std::all_of(hv.begin(), hv.end(), [](double x) { return x >= 0.0; });
   CK(c, cudaMemcpyAsync(c->mval[mb], hv.data(), sizeof(double) * e0, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaMemsetAsync(&c->dc->means_negative[mb], 0, sizeof(unsigned), c->stream));
   CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 0,
-                              c->stream));
+                              &c->dc->means_negative[mb], c->stream));
   ST(finish_set_means(c));
   c->iteration = iteration;
   return IVF_OK;
@@ -1108,7 +1167,6 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
     }
     for (int32_t j = c->h_inst_clu[b]; j < c->h_inst_clu[b + 1]; ++j) ids[j] += (int32_t)c->h_inst_docs[b];
   }
-  c->means_nonneg = true;  // the means are objects, whose sign is known
   // row lengths on the host to size the means
   std::vector<int64_t> hrp(c->N + 1);
   CK(c, cudaMemcpy(hrp.data(), c->row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToHost));
@@ -1122,8 +1180,9 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
                            c->temp, c->stream, 0));
   CK(c, launch_gather_rows(c->Kt, d_ids, c->row_ptr, c->term, c->val32, c->mptr[mb], c->mterm[mb], c->mval[mb],
                            c->temp, c->stream, 1));
+  CK(c, cudaMemsetAsync(&c->dc->means_negative[mb], 0, sizeof(unsigned), c->stream));
   CK(c, launch_normalise_rows(c->Kt, c->mptr[mb], c->mval[mb], c->mclu[mb], c->Dt, c->mterm[mb], &c->dc->status, 1,
-                              c->stream));
+                              &c->dc->means_negative[mb], c->stream));
   return finish_set_means(c);
 }
 
@@ -1274,6 +1333,7 @@ ivf_status ivf_get_info(ivf_ctx* c, ivf_info* out) {
   out->storage = c->cfg.storage;
   out->device_bytes = c->bytes;
   out->dense_head_r = c->shape.head_r;
+  out->dense_head_sub = c->shape.head_sub;
   out->dense_head_theta = c->shape.head_theta;
   long long heads = 0;
   if (c->shape.head_r > 0) {

@@ -22,7 +22,8 @@ enum StatusBits : unsigned {
 
 // Everything the assignment kernel reads and writes.
 struct AssignArgs {
-  int64_t n_docs;
+  int64_t n_docs;          // work items: objects 0, s, 2s, ... (s = obj_stride) below n_docs * s
+  int32_t obj_stride = 1;  // 1 except when the autotuner times a strided sample
   const int64_t* row_ptr;  // [N+1]
   const int32_t* term;     // [nnz] global term ids
   const void* val;         // [nnz] storage type
@@ -50,24 +51,31 @@ struct AssignArgs {
   int32_t* flag_cnt;            // [N] candidates, -1 = overflow (all clusters)
   int32_t* flag_cand;           // [cand_slots * CAND_MAX]
   int64_t cand_slots;           // flagged objects that get a candidate list
-  int32_t nonneg;               // all object values and mean values are >= 0
+  // The relative error bound for non-negative data applies when nonneg != 0
+  // and neither device flag (some object value < 0, some mean value < 0) is set.
+  int32_t nonneg;
+  const unsigned* negative;        // objects, or null
+  const unsigned* means_negative;  // the means the inverted file was built from, or null
   // Dense head rows (the IFN form for the densest posting lists): term t with
   // head_slot[t] >= 0 is read from wd[head_slot[t] * kpad + cluster] instead
   // of its sparse list.  Used by the register-accumulator kernels (head_r > 0).
   const int32_t* head_slot;     // [D] or null
   const void* wd;               // [T * kpad] storage type
-  int64_t kpad;                 // row length, a multiple of the tile (32 * head_r)
+  int64_t kpad;                 // row length, a multiple of the head sub-tile (32 * head_r)
+  int32_t head_sub = 1;         // head sub-tiles of 32 * head_r clusters per shared-memory tile
 };
 
 // Registers per lane of the head accumulator; the tile is 32 * R clusters.
 constexpr int HEAD_R_SMALL = 8;
+constexpr int HEAD_R_MID = 16;
 constexpr int HEAD_R_LARGE = 32;
 constexpr int HEAD_MAX_WARPS = 8;  // warps per block of the dense-head kernels
 
 size_t assign_smem_bytes(int tile_cap, int warps);
-cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r = 0);
+cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r = 0, int head_sub = 1);
+// head_sub > 1 (split dense-head kernel) is available for head_r == HEAD_R_LARGE only.
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r = 0);
-int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r = 0);
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r = 0, int head_sub = 1);
 // FP32 storage, untiled, int32 cluster ids (the caller-held inverted file of ivf_assign_static).
 cudaError_t assign_prepare_i32ids(int tile_cap, int warps);
 int assign_max_blocks_per_sm_i32ids(int tile_cap, int warps);
@@ -157,6 +165,7 @@ struct UpdateArgs {
   int64_t* d_u;         // number of unique (cluster, term) keys
   void* temp;           // radix / scan scratch
   unsigned* status;
+  unsigned* means_negative;  // set when a written mean value is negative (zeroed by the caller)
 };
 cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s);
 
@@ -201,10 +210,11 @@ cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s);
 
 // Means from rows: validate cluster-major rows, fill the row owner of every
 // entry and (normalise != 0) divide each row by its FP64 L2 norm in place;
-// a zero-norm row (when normalising) or a bad term sets STS_BAD_MEANS.
+// a zero-norm row (when normalising) or a bad term sets STS_BAD_MEANS, a
+// negative value sets *negative.
 cudaError_t launch_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu,
                                   int64_t dt, const int32_t* mterm, unsigned* status, int normalise,
-                                  cudaStream_t s);
+                                  unsigned* negative, cudaStream_t s);
 // Gather object rows d_ids[j] (global object ids) as mean rows (values promoted to FP64).
 cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t* row_ptr,
                                const int32_t* term, const float* val32, int64_t* lens_then_ptr,
@@ -218,5 +228,6 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                    unsigned* status, unsigned* negative, cudaStream_t s);
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
+cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s);
 
 }  // namespace ivfk

@@ -154,6 +154,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* keys, const 
   }
 }
 
+// Stable scatter of one 8-bit digit.  Each warp ranks its 16 x 32 keys with
+// match_any (in input order), the block turns the per-warp counts into
+// block-local positions, stages keys and values in shared memory in digit
+// order, and then writes each digit's run with consecutive threads on
+// consecutive addresses (coalesced), at the run's global offset.
 template <typename K>
 __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restrict__ kin,
                                                               const uint32_t* __restrict__ vin,
@@ -161,10 +166,15 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
                                                               const int64_t* d_n, int shift,
                                                               const uint32_t* __restrict__ offs, int64_t nb) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
-  __shared__ uint32_t dbase[RS_BINS];
+  __shared__ uint32_t dbase[RS_BINS];   // global start of the block's run of digit d
+  __shared__ uint32_t lbase[RS_BINS];   // block-local start of digit d
+  extern __shared__ __align__(16) unsigned char rs_stage[];
+  K* sk = reinterpret_cast<K*>(rs_stage);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(rs_stage + sizeof(K) * RS_TILE);
   const int64_t n = *d_n;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   if (base >= n) return;  // uniform over the block
+  const int cnt = (int)(n - base < RS_TILE ? n - base : RS_TILE);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
@@ -190,6 +200,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
     __syncwarp();
   }
   __syncthreads();
+  // per digit: warp offsets inside the digit, and the digit's block total
+  uint32_t tot = 0;
   for (int d = threadIdx.x; d < RS_BINS; d += RS_THREADS) {
     uint32_t acc = 0;
 #pragma unroll
@@ -198,7 +210,24 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
       wcnt[w][d] = acc;
       acc += c;
     }
+    tot = acc;
     dbase[d] = offs[(int64_t)d * nb + blockIdx.x];
+  }
+  // block-local digit starts: exclusive scan of the totals (RS_BINS == RS_THREADS)
+  {
+    static_assert(RS_BINS == RS_THREADS, "one digit per thread");
+    uint32_t x = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(IVF_FULL_MASK, x, o);
+      if (lane >= o) x += y;
+    }
+    __shared__ uint32_t wsum[RS_WARPS];
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += wsum[w];
+    lbase[threadIdx.x] = add + x - tot;
   }
   __syncthreads();
 #pragma unroll
@@ -206,11 +235,24 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_scatter(const K* __restric
     const int64_t idx = wbase + r * 32 + lane;
     if (idx < n) {
       const uint32_t d = (uint32_t)(k[r] >> shift) & 255u;
-      const uint32_t pos = dbase[d] + wcnt[warp][d] + rk[r];
-      kout[pos] = k[r];
-      vout[pos] = v[r];
+      const uint32_t lp = lbase[d] + wcnt[warp][d] + rk[r];
+      sk[lp] = k[r];
+      sv[lp] = v[r];
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += RS_THREADS) {
+    const K key = sk[i];
+    const uint32_t d = (uint32_t)(key >> shift) & 255u;
+    const uint32_t pos = dbase[d] + ((uint32_t)i - lbase[d]);
+    kout[pos] = key;
+    vout[pos] = sv[i];
+  }
+}
+
+template <typename K>
+constexpr size_t scatter_smem_bytes() {
+  return (sizeof(K) + sizeof(uint32_t)) * RS_TILE;
 }
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -232,7 +274,8 @@ cudaError_t radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
     k_radix_hist<K><<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, d_n, shift, hist, nb);
     IVF_LAUNCH_CHECK();
     IVF_CU(exclusive_scan_u32(hist, hist, (int64_t)RS_BINS * nb, scan_tmp, s));
-    k_radix_scatter<K><<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, vi, ko, vo, d_n, shift, hist, nb);
+    k_radix_scatter<K><<<(unsigned)nb, RS_THREADS, scatter_smem_bytes<K>(), s>>>(ki, vi, ko, vo, d_n, shift,
+                                                                                 hist, nb);
     IVF_LAUNCH_CHECK();
     K* tk = ki;
     ki = ko;
@@ -246,6 +289,14 @@ cudaError_t radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
 }
 
 }  // namespace
+
+cudaError_t radix_prepare() {
+  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)scatter_smem_bytes<uint64_t>()));
+  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)scatter_smem_bytes<uint32_t>()));
+  return cudaSuccess;
+}
 
 size_t scan_temp_bytes(int64_t n) { return ((size_t)ceil_div(n < 1 ? 1 : n, SCAN_CHUNK) + 2) * sizeof(int64_t); }
 

@@ -22,7 +22,10 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void*
 // low `bits` bits of the key.  Buffers ping-pong between (keys, vals) and
 // (keys_alt, vals_alt); *in_alt reports where the result ends up (a function
 // of `bits` only, so it is the same at every graph replay).
+// radix_prepare() opts the scatter kernels in to their shared-memory staging
+// area; call it once per process (per device) before the first sort.
 size_t radix_temp_bytes(int64_t n_max);
+cudaError_t radix_prepare();
 cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                            const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
                            bool* in_alt);

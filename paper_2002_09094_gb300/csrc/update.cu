@@ -10,12 +10,16 @@
 //      (cluster(i), term); a stable LSD radix sort brings equal keys together
 //      in ascending object id, and each run is summed sequentially in FP64
 //      (the same order in which the oracle's dense accumulation adds them);
-//   A7 normalise: ||s_j|| accumulated in ascending term order (separate
-//      multiply and add, no contraction), zero sums dropped (w_p != 0),
+//   A7 normalise: ||s_j||^2 by a block per cluster in a fixed order (strided
+//      partial sums, then a fixed tree; separate multiply and add, no
+//      contraction), zero sums dropped (w_p != 0) and the kept ones ranked
+//      by one device-wide scan,
 //      empty clusters keep their previous mean or become empty;
 //   A8 inverted file: a stable radix sort by term of the cluster-major means
 //      gives posting lists in ascending cluster id; term_ptr by binary search.
 // Dividing by |C_j| before normalising only rescales, so it is skipped.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "radix.cuh"
@@ -148,86 +152,115 @@ __global__ void k_uptr(UpdateArgs a) {
     a.uptr[j] = lower_bound_dev<uint64_t>(a.ukey, u_n, (uint64_t)j << a.tbits);
 }
 
-// Warp per cluster: ||s_j||^2 in ascending term order, count of nonzero
-// elements, and the length of the new mean row.  Lanes load and square 32
-// consecutive sums; the additions then run in the same sequential order as a
-// one-thread loop (every lane walks the same shuffled chain), so the result
-// does not depend on the launch shape.
-__global__ void k_cluster_norm(UpdateArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t j = gw; j < a.kt; j += nw) {
+// Block per cluster: ||s_j||^2, the count of nonzero elements and the
+// length of the new mean row.  Thread t sums the squares of elements
+// u0 + t, u0 + t + 256, ... in order; the 32 lanes of a warp are combined by
+// a fixed butterfly and the 8 warp totals in warp order.  The order depends
+// only on the cluster's element range, never on the launch shape, so the
+// result is bit-reproducible; long rows take E_j / 256 dependent steps.
+constexpr int kNormThreads = 256;
+__global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
+  __shared__ double wsum[kNormThreads / 32];
+  __shared__ int wnz[kNormThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t j = blockIdx.x; j < a.kt; j += gridDim.x) {
     const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
     double n2 = 0.0;
     int nz = 0;
-    for (int64_t ub = u0; ub < u1; ub += 32) {
-      const int64_t u = ub + lane;
-      double sq = 0.0;
-      if (u < u1) {
-        const double s = a.usum[u];
-        sq = __dmul_rn(s, s);
-        nz += (s != 0.0) ? 1 : 0;
-      }
-      const int cnt = (int)min((int64_t)32, u1 - ub);
-      for (int q = 0; q < cnt; ++q) n2 = __dadd_rn(n2, __shfl_sync(IVF_FULL_MASK, sq, q));
+    for (int64_t u = u0 + threadIdx.x; u < u1; u += kNormThreads) {
+      const double v = a.usum[u];
+      n2 = __dadd_rn(n2, __dmul_rn(v, v));
+      nz += (v != 0.0) ? 1 : 0;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(IVF_FULL_MASK, nz, o);
+    for (int o = 16; o > 0; o >>= 1) {
+      n2 = __dadd_rn(n2, __shfl_xor_sync(IVF_FULL_MASK, n2, o));
+      nz += __shfl_xor_sync(IVF_FULL_MASK, nz, o);
+    }
     if (lane == 0) {
-      const double nrm = __dsqrt_rn(n2);
+      wsum[warp] = n2;
+      wnz[warp] = nz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      int64_t cnt = 0;
+      for (int w = 0; w < kNormThreads / 32; ++w) {
+        t = __dadd_rn(t, wsum[w]);
+        cnt += wnz[w];
+      }
+      const double nrm = __dsqrt_rn(t);
       a.sum_norm[j] = nrm;
       int64_t len;
       if (nrm > 0.0)
-        len = nz;
+        len = cnt;
       else
         len = a.empty_policy == 0 ? (a.mptr_old[j + 1] - a.mptr_old[j]) : 0;
       a.newlen[j] = len;
     }
+    __syncthreads();
   }
 }
 
-// Warp per cluster: write mu_j = s_j / ||s_j|| (nonzero elements, in term
-// order) or the kept previous row.
-__global__ void k_write_means(UpdateArgs a) {
+// Keep flags of the run sums (every nonzero sum), scanned into output ranks
+// by the caller; flags[u] for u < nnz (the scan writes the total at nnz).
+__global__ void k_keep_flags(UpdateArgs a) {
+  const int64_t u_n = *a.d_u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.nnz; u += stride)
+    a.flags[u] = (u < u_n && a.usum[u] != 0.0) ? 1u : 0u;
+}
+
+// Thread per run sum: mu_j element = s / ||s_j|| at mptr_new[j] + (its rank
+// among the kept sums of cluster j), so each row stays in term order.
+__global__ void k_write_entries(UpdateArgs a) {
+  const int64_t e_new = a.mptr_new[a.kt];
+  if (e_new > a.cap) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, (unsigned)STS_CAPACITY);
+    return;
+  }
+  const int64_t u_n = *a.d_u;
+  const int tb = a.tbits;
+  const uint64_t tmask = (tb >= 64) ? ~0ull : ((1ull << tb) - 1ull);
+  bool neg = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
+    const double s = a.usum[u];
+    if (s == 0.0) continue;
+    const uint64_t key = a.ukey[u];
+    const int64_t j = (int64_t)(key >> tb);
+    const double nrm = a.sum_norm[j];
+    if (!(nrm > 0.0)) continue;
+    const int64_t o = a.mptr_new[j] + (int64_t)(a.flags[u] - a.flags[a.uptr[j]]);
+    a.mterm_new[o] = (int32_t)(key & tmask);
+    a.mval_new[o] = __ddiv_rn(s, nrm);
+    a.mclu_new[o] = (int32_t)j;
+    neg |= s < 0.0;
+  }
+  if (__any_sync(IVF_FULL_MASK, neg) && (threadIdx.x & 31) == 0) atomicOr(a.means_negative, 1u);
+}
+
+// Warp per cluster with no members (or a zero sum) under empty_policy 0:
+// copy the previous row.
+__global__ void k_copy_kept(UpdateArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t e_new = a.mptr_new[a.kt];
-  if (e_new > a.cap) {
-    if (gw == 0 && lane == 0) atomicOr(a.status, (unsigned)STS_CAPACITY);
-    return;
-  }
-  const uint64_t tmask = (a.tbits >= 64) ? ~0ull : ((1ull << a.tbits) - 1ull);
-  const unsigned lt = (1u << lane) - 1u;
+  if (a.empty_policy != 0 || a.mptr_new[a.kt] > a.cap) return;
+  bool neg = false;
   for (int64_t j = gw; j < a.kt; j += nw) {
-    const double nrm = a.sum_norm[j];
-    int64_t dst = a.mptr_new[j];
-    if (nrm > 0.0) {
-      const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
-      for (int64_t ub = u0; ub < u1; ub += 32) {
-        const int64_t u = ub + lane;
-        double s = 0.0;
-        if (u < u1) s = a.usum[u];
-        const bool keep = (u < u1) && (s != 0.0);
-        const unsigned km = __ballot_sync(IVF_FULL_MASK, keep);
-        if (keep) {
-          const int64_t o = dst + __popc(km & lt);
-          a.mterm_new[o] = (int32_t)(a.ukey[u] & tmask);
-          a.mval_new[o] = __ddiv_rn(s, nrm);
-          a.mclu_new[o] = (int32_t)j;
-        }
-        dst += __popc(km);
-      }
-    } else if (a.empty_policy == 0) {
-      const int64_t o0 = a.mptr_old[j], o1 = a.mptr_old[j + 1];
-      for (int64_t q = lane; q < o1 - o0; q += 32) {
-        a.mterm_new[dst + q] = a.mterm_old[o0 + q];
-        a.mval_new[dst + q] = a.mval_old[o0 + q];
-        a.mclu_new[dst + q] = (int32_t)j;
-      }
+    if (a.sum_norm[j] > 0.0) continue;
+    const int64_t dst = a.mptr_new[j];
+    const int64_t o0 = a.mptr_old[j], o1 = a.mptr_old[j + 1];
+    for (int64_t q = lane; q < o1 - o0; q += 32) {
+      a.mterm_new[dst + q] = a.mterm_old[o0 + q];
+      const double v = a.mval_old[o0 + q];
+      a.mval_new[dst + q] = v;
+      a.mclu_new[dst + q] = (int32_t)j;
+      neg |= !(v >= 0.0);
     }
   }
+  if (__any_sync(IVF_FULL_MASK, neg) && lane == 0) atomicOr(a.means_negative, 1u);
 }
 
 // ------------------------------------------------------- A8 inverted file
@@ -348,14 +381,16 @@ __global__ void k_head_fill(IvfBuildArgs a) {
 // ------------------------------------------------------ means from rows
 
 __global__ void k_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu, int64_t dt,
-                                 const int32_t* mterm, unsigned* status, int normalise) {
+                                 const int32_t* mterm, unsigned* status, int normalise, unsigned* negative) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < kt; j += stride) {
     const int64_t r0 = mptr[j], r1 = mptr[j + 1];
     double n2 = 0.0;
     bool ok = r1 >= r0;
+    bool neg = false;
     for (int64_t e = r0; e < r1; ++e) {
       const double v = mval[e];
+      neg |= !(v >= 0.0);
       n2 = __dadd_rn(n2, __dmul_rn(v, v));
       const int32_t t = mterm[e];
       if (t < 0 || (int64_t)t >= dt || (e > r0 && mterm[e - 1] >= t) || !isfinite(v)) ok = false;
@@ -364,6 +399,7 @@ __global__ void k_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, 
       atomicOr(status, (unsigned)STS_BAD_MEANS);
       continue;
     }
+    if (neg) atomicOr(negative, 1u);
     const double nrm = __dsqrt_rn(n2);
     for (int64_t e = r0; e < r1; ++e) {
       if (normalise) mval[e] = __ddiv_rn(mval[e], nrm);
@@ -440,6 +476,15 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_
   }
 }
 
+// row_ptr[0] == 0, non-decreasing, row_ptr[n] == nnz; a violation sets STS_BAD_ROWS.
+__global__ void k_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) bad |= rp[i + 1] < rp[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) bad |= rp[0] != 0 || rp[n] != nnz;
+  if (bad) atomicOr(status, (unsigned)STS_BAD_ROWS);
+}
+
 __global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
@@ -480,10 +525,15 @@ cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
   const unsigned gK = grid_for(a.kt + 1, T256, 8192);
   k_uptr<<<gK, T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
-  k_cluster_norm<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
+  k_cluster_norm<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
-  k_write_means<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
+  k_keep_flags<<<gE, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_u32(a.flags, a.flags, a.nnz, a.temp, s));  // flags[nnz] <- total
+  k_write_entries<<<gE, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  k_copy_kept<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }
@@ -546,14 +596,17 @@ cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_build_toff(const IvfBuildArgs& a, cudaStream_t s) {
+  if (a.toff == nullptr || a.k_tile <= 0) return cudaErrorInvalidValue;
   k_toff<<<grid_for(a.dt * (a.n_tiles_max + 1), T256, 16384), T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }
 
 cudaError_t launch_normalise_rows(int64_t kt, const int64_t* mptr, double* mval, int32_t* mclu, int64_t dt,
-                                  const int32_t* mterm, unsigned* status, int normalise, cudaStream_t s) {
-  k_normalise_rows<<<grid_for(kt, 64, 8192), 64, 0, s>>>(kt, mptr, mval, mclu, dt, mterm, status, normalise);
+                                  const int32_t* mterm, unsigned* status, int normalise, unsigned* negative,
+                                  cudaStream_t s) {
+  k_normalise_rows<<<grid_for(kt, 64, 8192), 64, 0, s>>>(kt, mptr, mval, mclu, dt, mterm, status, normalise,
+                                                         negative);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }
@@ -598,6 +651,12 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                                   inst_toff, inst_terms, validate, status, negative);
       break;
   }
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s) {
+  k_check_row_ptr<<<grid_for(n, T256, 4096), T256, 0, s>>>(rp, n, nnz, status);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -77,7 +77,8 @@ class Info(ctypes.Structure):
                 ("k", ctypes.c_int32), ("n_instances", ctypes.c_int32), ("ivf_entries", ctypes.c_int64),
                 ("ivf_capacity", ctypes.c_int64), ("k_tile", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("iteration", ctypes.c_int32), ("storage", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("dense_head_r", ctypes.c_int32), ("dense_head_theta", ctypes.c_float),
+                ("dense_head_r", ctypes.c_int32), ("dense_head_sub", ctypes.c_int32),
+                ("dense_head_theta", ctypes.c_float),
                 ("dense_head_rows", ctypes.c_int64)]
 
     def as_dict(self) -> dict:

@@ -53,7 +53,7 @@ def test_small_workload_ten_iterations_lockstep():
                 diverged = True
 
 
-@pytest.mark.parametrize("k_tile", [1024, 2048])
+@pytest.mark.parametrize("k_tile", [512, 1024, 2048])
 def test_tiled_accumulator_equals_untiled(k_tile):
     c = corpus_for(4000, 6000, mean_len=40.0)
     k = 3000
@@ -491,3 +491,128 @@ def test_means_capacity_grows_on_demand(use_graph):
     assert np.array_equal(out[0][0], out[1][0])
     for x, y in zip(out[0][1], out[1][1]):
         assert np.array_equal(x, y)
+
+
+# ------------------------------------------------ signs and reloaded objects
+
+
+def _signed(c, frac, seed):
+    """The corpus with a seeded fraction of its values negated (norms unchanged)."""
+    flip = np.random.default_rng(seed).random(c.nnz) < frac
+    val = np.where(flip, -c.val, c.val).astype(np.float32)
+    return dg.Corpus(c.row_ptr, c.term, val, c.n_terms)
+
+
+@pytest.mark.parametrize("kernel", ["sparse", "dense_head"])
+@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 2.5e-2)])
+def test_mixed_sign_objects_lockstep(kernel, storage, tol):
+    """Values of both signs: similarities can be negative, so unvisited
+    clusters (similarity 0) compete for the argmax, and the error bound of the
+    near-tie test is the absolute one."""
+    c = _signed(corpus_for(5000, 5000, mean_len=35.0, seed=31), 0.3, 31)
+    k = 1200
+    ids = dg.init_doc_ids(c.n_docs, k, 31)
+    for rep in lockstep(c, k, ids, 3, storage=storage, best_tol=tol, kernel=kernel):
+        assert_report_ok(rep)
+
+
+def test_negative_mean_rows_lockstep():
+    """Non-negative objects, caller means with negative values; empty
+    clusters keep their (negative) rows across the update."""
+    c = corpus_for(3000, 3000, mean_len=30.0, seed=32)
+    k = 200
+    rng = np.random.default_rng(32)
+    ptr = [0]
+    terms, vals = [], []
+    for _ in range(k):
+        t = np.sort(rng.choice(c.n_terms, 12, replace=False))
+        terms.append(t)
+        vals.append(rng.standard_normal(12))
+        ptr.append(ptr[-1] + 12)
+    rows = (np.array(ptr, np.int64), np.concatenate(terms).astype(np.int32),
+            np.concatenate(vals).astype(np.float32))
+    for rep in lockstep(c, k, None, 3, means_rows=rows):
+        assert_report_ok(rep)
+
+
+def test_load_objects_equals_fresh_context():
+    """Objects reloaded into a context (values of a different sign pattern)
+    give bit for bit what a context created on them gives."""
+    base = corpus_for(4000, 4000, mean_len=30.0, seed=33)
+    c2 = _signed(base, 0.4, 33)
+    k = 300
+    ids = dg.init_doc_ids(base.n_docs, k, 33)
+    out = []
+    with ivf.IVF(base.row_ptr, base.term, base.val, base.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        m.iterate(2)
+        m.load_objects(c2.row_ptr, c2.term, c2.val)
+        m.set_means_from_docs(ids)
+        m.iterate(2)
+        m.assign()
+        out.append((m.get_assign(), m.get_best(), m.get_gap()))
+        # and back to the non-negative objects
+        m.load_objects(base.row_ptr, base.term, base.val)
+        m.set_means_from_docs(ids)
+        m.assign()
+        out.append((m.get_assign(), m.get_best(), m.get_gap()))
+    for corpus, got in zip((c2, base), out):
+        with ivf.IVF(corpus.row_ptr, corpus.term, corpus.val, corpus.n_terms, k) as m:
+            m.set_means_from_docs(ids)
+            if corpus is c2:
+                m.iterate(2)
+            m.assign()
+            ref = (m.get_assign(), m.get_best(), m.get_gap())
+        for x, y in zip(got, ref):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+
+
+def test_load_objects_rejects_bad_row_ptr_and_stays_usable():
+    c = corpus_for(2000, 2000, mean_len=20.0, seed=34)
+    k = 50
+    ids = dg.init_doc_ids(c.n_docs, k, 34)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k) as m:
+        m.set_means_from_docs(ids)
+        m.assign()
+        a0 = m.get_assign()
+        shifted = c.row_ptr + 1                 # does not start at 0
+        decreasing = c.row_ptr.copy()
+        decreasing[5] = decreasing[6] + 1       # row 5 ends before it starts
+        short = c.row_ptr.copy()
+        short[-1] -= 1                          # does not end at nnz
+        for bad in (shifted, decreasing, short):
+            with pytest.raises(ivf.IvfError) as e:
+                m.load_objects(bad, c.term, c.val)
+            assert e.value.status == ivf.IVF_E_INVALID
+        # the context still holds the original objects
+        m.assign()
+        assert np.array_equal(m.get_assign(), a0)
+
+
+@pytest.mark.parametrize("k", [1500, 4500])
+def test_dense_head_wide_tiles_bit_equal(k):
+    """Shared-memory tiles of 1, 2 and 4 head sub-tiles (the sparse lists
+    scattered once per wide tile, the dense rows per 1,024-cluster sub-tile)
+    sum every rho_c in the same order, so their results are identical; K =
+    1,500 with a 2,048 tile runs untiled, K = 4,500 ends in a ragged tile."""
+    c = corpus_for(5000, 5000, mean_len=40.0, seed=k + 7)
+    ids = dg.init_doc_ids(c.n_docs, k, k + 7)
+    out = {}
+    for kt in (1024, 2048, 4096):
+        if kt == 4096 and k <= 2048:
+            continue
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel="dense_head", k_tile=kt) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(2)
+            st = m.assign()
+            inf = m.info()
+            assert inf["dense_head_r"] == 32 and inf["dense_head_sub"] == kt // 1024
+            out[kt] = (m.get_assign(), m.get_best(), m.get_gap(), st["entries_visited"])
+    ref = out[1024]
+    for kt, got in out.items():
+        for x, y in zip(got[:3], ref[:3]):
+            assert np.array_equal(x.view(np.uint32), y.view(np.uint32)), kt
+        assert got[3] == ref[3]
+    wide = max(out)
+    for rep in lockstep(c, k, ids, 2, kernel="dense_head", k_tile=wide):
+        assert_report_ok(rep)
