@@ -105,12 +105,14 @@ int alg3_assign(int64_t n_docs, const int64_t* row_ptr, const int32_t* term, con
 /* Update step.  Outputs the new inverted file: out_ptr[n_terms + 1] and up to
  * out_cap tuples in out_c / out_u.  Returns ALG3_E_OOM (with *out_len set to
  * the length needed) when out_cap is too small.  prev_* is the inverted file
- * the assignment used (for empty_policy 0). */
+ * the assignment used (for empty_policy 0).  Only clusters j0 <= j < j1 get
+ * rows (the whole update is j0 = 0, j1 = k; a range times a sample of it). */
 int alg3_update(int64_t n_docs, const int64_t* row_ptr, const int32_t* term, const float* val, int32_t k,
                 int64_t n_terms, const int32_t* assign, const int64_t* prev_ptr, const int32_t* prev_c,
-                const double* prev_u, int32_t empty_policy, int64_t* out_ptr, int32_t* out_c, double* out_u,
-                int64_t out_cap, int64_t* out_len, int threads) {
+                const double* prev_u, int32_t empty_policy, int32_t j0, int32_t j1, int64_t* out_ptr,
+                int32_t* out_c, double* out_u, int64_t out_cap, int64_t* out_len, int threads) {
   if (k < 1 || n_terms < 1 || !assign || !out_ptr || !out_len) return ALG3_E_INVALID;
+  if (j0 < 0 || j1 > k || j0 > j1) return ALG3_E_INVALID;
   const int nt = n_threads_for(threads);
   int status = ALG3_OK;
   /* C_j in ascending object id (a stable counting sort of the objects) */
@@ -173,7 +175,7 @@ int alg3_update(int64_t n_docs, const int64_t* row_ptr, const int32_t* term, con
       status = ALG3_E_OOM;
     } else {
 #pragma omp for schedule(dynamic, 4)
-      for (int32_t j = 0; j < k; ++j) {
+      for (int32_t j = j0; j < j1; ++j) {
         for (int64_t p = 0; p < n_terms; ++p) w[p] = 0.0;
         const int64_t size = cl_ptr[j + 1] - cl_ptr[j];
         for (int64_t q = cl_ptr[j]; q < cl_ptr[j + 1]; ++q) {

@@ -44,7 +44,8 @@ def _load():
         vp, i64, i32, cint = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
         lib.alg3_assign.argtypes = [i64, vp, vp, vp, i32, i64, vp, vp, vp, vp, i64, vp, vp, vp, cint]
         lib.alg3_assign.restype = cint
-        lib.alg3_update.argtypes = [i64, vp, vp, vp, i32, i64, vp, vp, vp, vp, i32, vp, vp, vp, i64, vp, cint]
+        lib.alg3_update.argtypes = [i64, vp, vp, vp, i32, i64, vp, vp, vp, vp, i32, i32, i32, vp, vp, vp, i64, vp,
+                                    cint]
         lib.alg3_update.restype = cint
         lib.alg3_threads_available.argtypes = []
         lib.alg3_threads_available.restype = cint
@@ -108,8 +109,10 @@ def assignment_step(corpus, xi: InvertedFile, k: int, rows=None, threads: int = 
 
 
 def update_step(corpus, assign, k: int, prev: InvertedFile | None = None, empty_policy: int = 0,
-                threads: int = 0) -> InvertedFile:
-    """Algorithm 3's update: the new inverted file from the assignment."""
+                threads: int = 0, clusters: tuple[int, int] | None = None) -> InvertedFile:
+    """Algorithm 3's update: the new inverted file from the assignment
+    (clusters = (j0, j1): only those clusters' rows, for timing a sample)."""
+    j0, j1 = (0, int(k)) if clusters is None else (int(clusters[0]), int(clusters[1]))
     rp, tm, vl = _corpus_arrays(corpus)
     a = np.ascontiguousarray(assign, dtype=np.int32)
     out_ptr = np.empty(corpus.n_terms + 1, dtype=np.int64)
@@ -119,7 +122,8 @@ def update_step(corpus, assign, k: int, prev: InvertedFile | None = None, empty_
     out_len = ctypes.c_int64(0)
     st = _load().alg3_update(corpus.n_docs, _p(rp), _p(tm), _p(vl), int(k), int(corpus.n_terms), _p(a),
                              _p(prev.ptr) if prev else None, _p(prev.c) if prev else None,
-                             _p(prev.u) if prev else None, int(empty_policy), _p(out_ptr), _p(out_c), _p(out_u),
+                             _p(prev.u) if prev else None, int(empty_policy), j0, j1, _p(out_ptr), _p(out_c),
+                             _p(out_u),
                              int(cap), ctypes.byref(out_len), int(threads))
     if st != 0:
         raise RuntimeError(f"alg3_update failed with status {st}")

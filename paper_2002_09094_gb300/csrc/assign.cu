@@ -310,8 +310,11 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
     };
     // The dense head rows of one chunk, two at a time (ascending term order
     // per cluster): acc[g*VEC+k] += v * w[slo + VEC*(32g + lane) + k].
+    // NR rows per round (two FP32 rows, or four 16-bit rows: the same bytes
+    // in flight per lane, twice the work per round for 16-bit storage).
+    constexpr int NR = sizeof(WT) == 4 ? 2 : 4;
     auto head_rows = [&](unsigned hm, int slot, float v, int slo, int ng_live) {
-      if constexpr (R > 0) {
+      if constexpr (R > 0 && NR == 2) {
         while (hm) {
           const int j0 = __ffs(hm) - 1;
           hm &= hm - 1;
@@ -324,8 +327,10 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
           const float v1 = two ? __shfl_sync(IVF_FULL_MASK, v, j1) : 0.f;  // fma(0, w, acc) == acc
           const uint4* __restrict__ row0 = reinterpret_cast<const uint4*>(wd + (int64_t)s0 * a.kpad + slo) + lane;
           const uint4* __restrict__ row1 = reinterpret_cast<const uint4*>(wd + (int64_t)s1 * a.kpad + slo) + lane;
-          // groups that lie wholly past the sub-tile's last cluster are
-          // skipped (warp-uniform), so a small K does not pay for the full width
+          // groups that lie wholly past the sub-tile's last cluster are not
+          // summed (warp-uniform); their loads stay unconditional, which keeps
+          // the register count at the budget (re-pointing them at group 0 cost
+          // spills and 10 % of the FP32 assignment)
           uint4 w0[NG], w1[NG];
 #pragma unroll
           for (int g = 0; g < NG; ++g) w0[g] = __ldg(row0 + 32 * g);
@@ -347,6 +352,43 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
               unpack16<WT>(w1[g], e);
 #pragma unroll
               for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = fmaf(v1, e[k], acc[g * VEC + k]);
+            }
+          }
+        }
+      } else if constexpr (R > 0) {
+        while (hm) {
+          // the next NR dense rows of the chunk, in ascending term order; a
+          // missing row repeats the first with v = 0 (fma(0, w, acc) == acc)
+          int sr[NR];
+          float vr[NR];
+          const int j0 = __ffs(hm) - 1;
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const bool have = hm != 0;
+            const int j = have ? __ffs(hm) - 1 : j0;
+            if (have) hm &= hm - 1;
+            sr[r] = __shfl_sync(IVF_FULL_MASK, slot, j);
+            const float vv = __shfl_sync(IVF_FULL_MASK, v, j);
+            vr[r] = have ? vv : 0.f;
+          }
+          // groups past the sub-tile's last cluster: not summed, loads re-read group 0
+          uint4 wr[NR][NG];
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+            const uint4* __restrict__ row = reinterpret_cast<const uint4*>(wd + (int64_t)sr[r] * a.kpad + slo) + lane;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) wr[r][g] = __ldg(row + 32 * (g < ng_live ? g : 0));
+          }
+#pragma unroll
+          for (int r = 0; r < NR; ++r) {
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              if (g < ng_live) {
+                float e[VEC];
+                unpack16<WT>(wr[r][g], e);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = fmaf(vr[r], e[k], acc[g * VEC + k]);
+              }
             }
           }
         }

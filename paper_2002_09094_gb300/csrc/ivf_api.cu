@@ -697,10 +697,12 @@ ivf_status autotune(ivf_ctx* c) {
       // wider shared-memory tiles for the sparse lists (fewer, longer
       // per-tile slices when K spans many head sub-tiles)
       for (int sub : {2, 4})
-        for (int wp : {4, 8}) {
-          if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
-          if (shape_for(c, 0, wp, &sh, HEAD_R_LARGE, 0.25f, sub)) cands.push_back(sh);
-        }
+        for (float theta : {0.25f, 0.125f})
+          for (int wp : {4, 8}) {
+            if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
+            if (theta < 0.25f && wp != 4) continue;
+            if (shape_for(c, 0, wp, &sh, HEAD_R_LARGE, theta, sub)) cands.push_back(sh);
+          }
     }
   }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");

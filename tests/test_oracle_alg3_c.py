@@ -105,3 +105,15 @@ def test_invalid_inputs_are_statuses():
         calg3.assignment_step(c, xi, 3, rows=np.array([0, 20]))
     with pytest.raises(RuntimeError):
         calg3.update_step(c, np.full(c.n_docs, 3, np.int32), 3)
+
+
+def test_cluster_range_update_is_the_slice_of_the_full_update():
+    c = small_corpus(46, n_docs=200, n_terms=90)
+    k = 10
+    m0 = sk.initial_means(c, dg.init_doc_ids(c.n_docs, k, 46))
+    xi = calg3.InvertedFile.from_means(m0)
+    a, _, _ = calg3.assignment_step(c, xi, k)
+    full = calg3.update_step(c, a, k, prev=xi)
+    part = calg3.update_step(c, a, k, prev=xi, clusters=(3, 7))
+    sel = (full.c >= 3) & (full.c < 7)
+    assert np.array_equal(part.c, full.c[sel]) and np.array_equal(part.u, full.u[sel])
