@@ -88,6 +88,10 @@ typedef struct {
   uint32_t flags;      /* IVF_FLAG_* */
   int32_t means_capacity; /* entries reserved for the means / inverted file at create
                              (0 = automatic); the arrays grow on demand */
+  int64_t dense_head_bytes; /* device memory first reserved for dense head rows
+                               (0 = 2 GiB); grows on demand up to 24 GiB when more
+                               lists qualify (the lists that do not fit are read
+                               from the sparse inverted file: exact, slower) */
 } ivf_config;
 
 /* Per-iteration statistics (Section 5.2 reports time and memory per

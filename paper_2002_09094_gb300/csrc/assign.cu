@@ -229,8 +229,17 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
     if (lane == 0) o = atomicAdd(a.work, 1ull);
     o = __shfl_sync(IVF_FULL_MASK, o, 0);
     if (o >= (unsigned long long)a.n_docs) break;
-    const int64_t i = (int64_t)o * a.obj_stride;
-    const int b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
+    const int64_t oi = (int64_t)o * a.obj_stride;
+    int64_t i;
+    int b;
+    if (a.obj_inst != nullptr) {
+      const int q = find_instance(a.obj_prefix, a.n_obj_inst, oi);
+      b = a.obj_inst[q];
+      i = a.inst_docs[b] + (oi - a.obj_prefix[q]);
+    } else {
+      i = oi;
+      b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
+    }
     const int K = a.inst_clu[b + 1] - a.inst_clu[b];
     const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
     const int m = (int)(r1 - r0);

@@ -32,6 +32,7 @@ struct DevCounters {
   unsigned long long work;
   unsigned long long entries;
   unsigned long long n_rescored;
+  unsigned long long work_cls[4];   // work counters of the per-class launches (batched contexts)
   unsigned int n_flagged;
   unsigned int status;
   double objective;
@@ -42,6 +43,7 @@ struct DevCounters {
   long long heads;                  // dense head rows of the inverted file last built
   unsigned int negative;            // some object value is negative (not an error)
   unsigned int means_negative[2];   // some value of means buffer 0 / 1 is negative
+  long long heads_wanted;           // lists that qualified as dense rows in the last build
 };
 
 struct Shape {
@@ -55,11 +57,17 @@ struct Shape {
   float head_theta = 0.f;  // a list covering at least this fraction of K is stored densely
 };
 
-// Dense head rows may use at most this much device memory.
+// Dense head rows start with room for this much device memory and grow, when
+// more lists qualify, up to kHeadMaxBytes.
 constexpr int64_t kHeadBudgetBytes = int64_t(2) << 30;
+constexpr int64_t kHeadMaxBytes = int64_t(24) << 30;
 
 std::mutex g_tune_mu;
-std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, Shape> g_tune_cache;
+struct TuneChoice {
+  Shape main;
+  std::vector<Shape> cls;  // batched contexts: the classes below the last one
+};
+std::map<std::tuple<int64_t, int64_t, int64_t, int, int>, TuneChoice> g_tune_cache;
 
 constexpr int kTileChoices[] = {1024, 2048, 4096, 8192, 16384, 32768};
 constexpr size_t kSmemBudget = 227 * 1024;
@@ -77,6 +85,7 @@ struct ivf_ctx {
   int32_t n_inst = 1;
   int32_t kmax = 0;
   int tbits = 1, kbits = 1;
+  int tbits_local = 1;  // bits of the largest instance's own term ids (update-step sort keys)
   int64_t cap = 0;  // capacity of means / inverted-file arrays
   int64_t e_cur = 0;
   std::vector<int64_t> h_inst_docs, h_inst_toff;
@@ -150,8 +159,21 @@ struct ivf_ctx {
   int64_t* d_u = nullptr;
   void* temp = nullptr;
   int64_t scratch_len = 0;
-  // launch shape
+  // launch shape (of the class holding the largest K in a batched context)
   Shape shape;
+  // Batched contexts: instances grouped by K (<= 512, <= 1,024, larger), one
+  // assignment launch per class, each with its own kernel; the last class
+  // holds the largest K and uses `shape` (the only one that may be tiled).
+  struct ClassPlan {
+    int32_t kmax = 0;
+    int64_t n_objs = 0;
+    std::vector<int32_t> insts;
+    int32_t* d_inst = nullptr;
+    int64_t* d_prefix = nullptr;
+    Shape shape;
+  };
+  std::vector<ClassPlan> cls;
+  bool use_classes = false;
   bool tuned = false;
   bool tuned_on_updated_means = false;  // the choice was made on means from an update step
   // state
@@ -341,6 +363,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   c->Dt = c->h_inst_toff[n_inst];
   c->tbits = bits_for(c->Dt);
   c->kbits = bits_for(c->Kt);
+  c->tbits_local = bits_for(*std::max_element(inst_terms.begin(), inst_terms.end()));
   if (c->tbits + c->kbits > 64) return bail(fail(c, IVF_E_UNSUPPORTED, "cluster and term ids need more than 64 bits"));
   if (c->N >= (int64_t(1) << 31) || c->Kt >= (int64_t(1) << 31) || c->Dt >= (int64_t(1) << 31))
     return bail(fail(c, IVF_E_UNSUPPORTED, "N, K and D must be below 2^31"));
@@ -392,6 +415,31 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->flag_obj, N);
   AL(c->flag_cnt, N);
   c->cand_slots = std::min<int64_t>(N, int64_t(1) << 20);
+  // batched: classes of instances by K (see ClassPlan); autotuned contexts only
+  if (n_inst > 1 && cfg->k_tile == 0 && cfg->warps_per_block == 0) {
+    const int32_t bounds[3] = {512, 1024, INT32_MAX};
+    for (int32_t lo = 0, q = 0; q < 3; lo = bounds[q], ++q) {
+      ivf_ctx::ClassPlan p;
+      std::vector<int64_t> prefix(1, 0);
+      for (int32_t b = 0; b < n_inst; ++b)
+        if (inst_k[b] > lo && inst_k[b] <= bounds[q]) {
+          p.insts.push_back(b);
+          prefix.push_back(prefix.back() + (inst_docs[b + 1] - inst_docs[b]));
+          p.kmax = std::max(p.kmax, inst_k[b]);
+        }
+      if (p.insts.empty()) continue;
+      p.n_objs = prefix.back();
+      AL(p.d_inst, (int64_t)p.insts.size());
+      AL(p.d_prefix, (int64_t)prefix.size());
+      e = cudaMemcpy(p.d_inst, p.insts.data(), sizeof(int32_t) * p.insts.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p.d_prefix, prefix.data(), sizeof(int64_t) * prefix.size(), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return bail(fail_cuda(c, "cudaMemcpy", e));
+      c->cls.push_back(std::move(p));
+    }
+    c->use_classes = c->cls.size() > 1;
+    if (!c->use_classes) c->cls.clear();
+  }
   AL(c->flag_cand, c->cand_slots * (int64_t)CAND_MAX);
   AL(c->dc, 1);
   c->d_e = reinterpret_cast<int64_t*>(&c->dc->ivf_e);
@@ -461,6 +509,7 @@ ivf_status validate_cfg(const ivf_config* cfg) {
   if (cfg->rescore != 0 && cfg->rescore != 1) return IVF_E_INVALID;
   if (cfg->warps_per_block < 0 || cfg->warps_per_block > 32) return IVF_E_INVALID;
   if (cfg->means_capacity < 0) return IVF_E_INVALID;
+  if (cfg->dense_head_bytes < 0) return IVF_E_INVALID;
   if (cfg->k_tile < 0) return IVF_E_INVALID;
   return IVF_OK;
 }
@@ -504,6 +553,7 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
     a.inst_toff = c->inst_toff;
     a.hflags = c->hflags;
     a.d_heads = reinterpret_cast<int64_t*>(&c->dc->heads);
+    a.d_heads_wanted = reinterpret_cast<int64_t*>(&c->dc->heads_wanted);
   }
   return a;
 }
@@ -520,7 +570,8 @@ ivf_status alloc_head(ivf_ctx* c, int head_r) {
   c->hflags = nullptr;
   c->wd = nullptr;
   const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
-  c->head_max = std::max<int64_t>(1, std::min<int64_t>(c->Dt, kHeadBudgetBytes / (kpad * vb)));
+  const int64_t budget = c->cfg.dense_head_bytes > 0 ? c->cfg.dense_head_bytes : kHeadBudgetBytes;
+  c->head_max = std::max<int64_t>(1, std::min<int64_t>(c->Dt, budget / (kpad * vb)));
   c->kpad = kpad;
   ST(dalloc(c, &c->head_slot, c->Dt));
   ST(dalloc(c, &c->hflags, c->Dt + 1));
@@ -528,6 +579,28 @@ ivf_status alloc_head(ivf_ctx* c, int head_r) {
   ST(dalloc(c, &p, c->head_max * kpad * vb));
   c->wd = p;
   drop_graphs(c);
+  return IVF_OK;
+}
+
+// When more lists qualified as dense rows in the last build (wanted) than
+// the rows hold, grow the rows (up to kHeadMaxBytes) and rebuild them from
+// the current means; the lists that did not fit were read sparsely, which is
+// exact but slower.  Synchronises only when it grows.
+ivf_status grow_head_if_needed(ivf_ctx* c, long long wanted) {
+  if (c->shape.head_r <= 0 || !c->head_slot || wanted <= c->head_max) return IVF_OK;
+  const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
+  const int64_t cap_rows = std::max<int64_t>(1, kHeadMaxBytes / (c->kpad * vb));
+  const int64_t rows = std::min<int64_t>({c->Dt, cap_rows, (int64_t)wanted + wanted / 4 + 64});
+  if (rows <= c->head_max) return IVF_OK;
+  CK(c, cudaStreamSynchronize(c->stream));
+  dfree(c, c->wd);
+  c->wd = nullptr;
+  char* p = nullptr;
+  ST(dalloc(c, &p, rows * c->kpad * vb));
+  c->wd = p;
+  c->head_max = rows;
+  drop_graphs(c);
+  CK(c, launch_build_head(ivf_args(c, c->mcur), c->stream));
   return IVF_OK;
 }
 
@@ -585,19 +658,19 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
 
 // head_r > 0 selects the dense-head kernel, whose shared-memory tile is
 // head_sub sub-tiles of 32 * head_r clusters.
-bool shape_for(ivf_ctx* c, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f,
+bool shape_for(ivf_ctx* c, int32_t kmax, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f,
                int head_sub = 1) {
   Shape sh;
   if (head_r > 0) {
     if (head_sub < 1 || !is_pow2(head_sub)) return false;
     k_tile = 32 * head_r * head_sub;
   }
-  if (k_tile <= 0 || k_tile >= c->kmax) {
-    if (c->kmax > 65536) return false;
-    if (head_r > 0 && head_sub > 1 && 32 * head_r * (head_sub / 2) >= c->kmax) return false;  // no gain
+  if (k_tile <= 0 || k_tile >= kmax) {
+    if (kmax > 65536) return false;
+    if (head_r > 0 && head_sub > 1 && 32 * head_r * (head_sub / 2) >= kmax) return false;  // no gain
     sh.tiled = 0;
-    sh.k_tile = c->kmax;
-    sh.tile_cap = (c->kmax + 3) & ~3;
+    sh.k_tile = kmax;
+    sh.tile_cap = (kmax + 3) & ~3;
   } else {
     if (!is_pow2(k_tile) || k_tile < (head_r > 0 ? 256 : 512) || k_tile > 65536) return false;
     sh.tiled = 1;
@@ -644,7 +717,87 @@ ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.head_r > 0) ST(alloc_head(c, sh.head_r));
   IvfBuildArgs a = ivf_args(c, c->mcur);
   if (sh.tiled) CK(c, launch_build_toff(a, c->stream));
-  if (sh.head_r > 0) CK(c, launch_build_head(a, c->stream));
+  if (sh.head_r > 0) {
+    CK(c, launch_build_head(a, c->stream));
+    long long wanted = 0;
+    CK(c, cudaMemcpyAsync(&wanted, &c->dc->heads_wanted, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    ST(grow_head_if_needed(c, wanted));
+  }
+  drop_graphs(c);
+  return IVF_OK;
+}
+
+// Work items of class q (q < 0: every object in order) for an assignment launch.
+void set_class_objs(ivf_ctx* c, AssignArgs& a, int q) {
+  if (q < 0) return;
+  const ivf_ctx::ClassPlan& p = c->cls[q];
+  a.obj_inst = p.d_inst;
+  a.obj_prefix = p.d_prefix;
+  a.n_obj_inst = (int32_t)p.insts.size();
+  a.n_docs = p.n_objs;
+  a.work = &c->dc->work_cls[q];
+}
+
+// Device time of one assignment (no re-score) with shape sh over class q's
+// objects (q < 0: all): large sets are timed on every s-th object (s <= 16,
+// at least 65,536 objects), a sample that spans every instance.
+ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
+  const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
+  AssignArgs a = assign_args(c, sh, target, 0);
+  set_class_objs(c, a, q);
+  const int64_t n = a.n_docs;
+  const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(16, n >> 16));
+  a.obj_stride = (int32_t)stride;
+  a.n_docs = (n + stride - 1) / stride;
+  float ms_min = 1e30f;
+  for (int rep = 0; rep < 2; ++rep) {
+    CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), c->stream));
+    CK(c, cudaEventRecord(c->ev[0], c->stream));
+    CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
+    CK(c, cudaEventRecord(c->ev[1], c->stream));
+    CK(c, cudaEventSynchronize(c->ev[1]));
+    float ms = 0.f;
+    CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    ms_min = std::min(ms_min, ms);
+  }
+  *ms_out = ms_min;
+  return IVF_OK;
+}
+
+// Kernels for the classes below the last one: untiled (their K fits one
+// tile), the sparse kernel or a dense-head kernel reading the rows built for
+// the main shape (same theta, register tile no wider than the main one's).
+ivf_status tune_classes(ivf_ctx* c) {
+  for (size_t q = 0; q + 1 < c->cls.size(); ++q) {
+    ivf_ctx::ClassPlan& p = c->cls[q];
+    std::vector<Shape> cands;
+    Shape sh;
+    const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0 || c->shape.head_r == 0;
+    const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0 && c->shape.head_r > 0;
+    if (!head_only && shape_for(c, p.kmax, 0, 0, &sh) && !sh.tiled) cands.push_back(sh);
+    if (!no_head)
+      for (int hr : {HEAD_R_SMALL, HEAD_R_MID, HEAD_R_LARGE})
+        for (int wp : {8, 4}) {
+          if (hr > c->shape.head_r) continue;
+          if (shape_for(c, p.kmax, 0, wp, &sh, hr, c->shape.head_theta) && !sh.tiled) cands.push_back(sh);
+        }
+    if (cands.empty()) cands.push_back(c->shape);  // cannot happen for K <= 1,024; kept for safety
+    Shape best = cands[0];
+    float best_ms = 1e30f;
+    for (const Shape& cand : cands) {
+      CK(c, assign_prepare(c->cfg.storage, cand.tile_cap, cand.warps, cand.head_r, cand.head_sub));
+      float ms = 0.f;
+      ST(time_shape(c, cand, (int)q, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cand;
+      }
+    }
+    CK(c, assign_prepare(c->cfg.storage, best.tile_cap, best.warps, best.head_r, best.head_sub));
+    p.shape = best;
+  }
+  c->cls.back().shape = c->shape;
   drop_graphs(c);
   return IVF_OK;
 }
@@ -663,9 +816,9 @@ ivf_status autotune(ivf_ctx* c) {
     if (c->cfg.flags & IVF_FLAG_DENSE_HEAD) {
       const int hr = c->cfg.k_tile < 32 * HEAD_R_LARGE ? HEAD_R_MID : HEAD_R_LARGE;
       ok = c->cfg.k_tile % (32 * hr) == 0 &&
-           shape_for(c, 0, c->cfg.warps_per_block, &sh, hr, 0.25f, c->cfg.k_tile / (32 * hr));
+           shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh, hr, 0.25f, c->cfg.k_tile / (32 * hr));
     } else {
-      ok = shape_for(c, c->cfg.k_tile, c->cfg.warps_per_block, &sh);
+      ok = shape_for(c, c->kmax, c->cfg.k_tile, c->cfg.warps_per_block, &sh);
     }
     if (!ok) return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
     cands.push_back(sh);
@@ -673,9 +826,9 @@ ivf_status autotune(ivf_ctx* c) {
     const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0;
     const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0;
     if (!head_only) {
-      if (shape_for(c, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+      if (shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
       for (int t : kTileChoices)
-        if (t < c->kmax && shape_for(c, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
+        if (t < c->kmax && shape_for(c, c->kmax, t, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
     }
     // dense-head kernels (the IFN form for lists covering >= theta K clusters)
     // 512- and 1,024-cluster tiles (fewer registers and more warps per SM
@@ -692,7 +845,7 @@ ivf_status autotune(ivf_ctx* c) {
           for (int wp : {8, 4}) {
             if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
             if (hr != HEAD_R_LARGE && wp != 8) continue;
-            if (shape_for(c, 0, wp, &sh, hr, theta)) cands.push_back(sh);
+            if (shape_for(c, c->kmax, 0, wp, &sh, hr, theta)) cands.push_back(sh);
           }
       // wider shared-memory tiles for the sparse lists (fewer, longer
       // per-tile slices when K spans many head sub-tiles)
@@ -701,7 +854,7 @@ ivf_status autotune(ivf_ctx* c) {
           for (int wp : {4, 8}) {
             if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
             if (theta < 0.25f && wp != 4) continue;
-            if (shape_for(c, 0, wp, &sh, HEAD_R_LARGE, theta, sub)) cands.push_back(sh);
+            if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_LARGE, theta, sub)) cands.push_back(sh);
           }
     }
   }
@@ -712,56 +865,44 @@ ivf_status autotune(ivf_ctx* c) {
   auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
                              (c->cfg.storage * 16 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
                              c->n_inst);
+  const bool cacheable = c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
-    if (it != g_tune_cache.end() && c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
-      ST(set_shape(c, it->second));
+    if (it != g_tune_cache.end() && cacheable) {
+      ST(set_shape(c, it->second.main));
+      for (size_t q = 0; q + 1 < c->cls.size() && q < it->second.cls.size(); ++q) c->cls[q].shape = it->second.cls[q];
+      if (!c->cls.empty()) c->cls.back().shape = c->shape;
       c->tuned = true;
       c->tuned_on_updated_means = c->iteration > 0;
       return IVF_OK;
     }
   }
-  if (cands.size() == 1) {
-    ST(set_shape(c, cands[0]));
-    c->tuned = true;
-    c->tuned_on_updated_means = c->iteration > 0;
-    return IVF_OK;
-  }
-  // Time one assignment per candidate (no re-score) on the real data.
-  const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
-  float best_ms = 1e30f;
+  const int main_q = c->use_classes ? (int)c->cls.size() - 1 : -1;
   Shape best_sh = cands[0];
-  for (const Shape& cand : cands) {
-    ST(set_shape(c, cand));
-    AssignArgs a = assign_args(c, cand, target, 0);
-    // Large problems are timed on every s-th object (s <= 16, at least 65,536
-    // objects): a sample that spans every instance of a batched context.
-    const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(16, c->N >> 16));
-    a.obj_stride = (int32_t)stride;
-    a.n_docs = (c->N + stride - 1) / stride;
-    float ms_min = 1e30f;
-    for (int rep = 0; rep < 2; ++rep) {
-      CK(c, cudaMemsetAsync(c->dc, 0, sizeof(unsigned long long) * 2, c->stream));
-      CK(c, cudaEventRecord(c->ev[0], c->stream));
-      CK(c, launch_assign(a, cand.warps, cand.blocks, c->stream, cand.head_r));
-      CK(c, cudaEventRecord(c->ev[1], c->stream));
-      CK(c, cudaEventSynchronize(c->ev[1]));
+  if (cands.size() > 1) {
+    // Time one assignment per candidate (no re-score) on the real data.
+    float best_ms = 1e30f;
+    for (const Shape& cand : cands) {
+      ST(set_shape(c, cand));
       float ms = 0.f;
-      CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
-      ms_min = std::min(ms_min, ms);
-    }
-    if (ms_min < best_ms) {
-      best_ms = ms_min;
-      best_sh = cand;
+      ST(time_shape(c, cand, main_q, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_sh = cand;
+      }
     }
   }
   ST(set_shape(c, best_sh));
+  if (c->use_classes) ST(tune_classes(c));
   c->tuned = true;
   c->tuned_on_updated_means = c->iteration > 0;
-  if (c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0) {
+  if (cacheable) {
+    TuneChoice tc;
+    tc.main = best_sh;
+    for (size_t q = 0; q + 1 < c->cls.size(); ++q) tc.cls.push_back(c->cls[q].shape);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_sh;
+    g_tune_cache[key] = tc;
   }
   return IVF_OK;
 }
@@ -784,10 +925,20 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
   cudaStream_t s = c->stream;
   CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), s));
   CK(c, cudaMemsetAsync(c->inst_changed, 0, sizeof(long long) * c->n_inst, s));
-  AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
   size_t e0 = 0, e1 = 0, e2 = 0;
   if (timed) CK(c, timing_event(c, &e0));
-  CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
+  if (c->use_classes) {
+    // one launch per class of instances, each with the kernel chosen for it
+    for (size_t q = 0; q < c->cls.size(); ++q) {
+      const Shape& sh = c->cls[q].shape;
+      AssignArgs a = assign_args(c, sh, target, c->cfg.rescore);
+      set_class_objs(c, a, (int)q);
+      CK(c, launch_assign(a, sh.warps, sh.blocks, s, sh.head_r));
+    }
+  } else {
+    AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
+    CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
+  }
   if (timed) CK(c, timing_event(c, &e1));
   if (c->cfg.rescore) {
     RescoreArgs r{};
@@ -845,8 +996,9 @@ ivf_status enqueue_update(ivf_ctx* c, int src) {
   u.n_inst = c->n_inst;
   u.kt = c->Kt;
   u.dt = c->Dt;
-  u.tbits = c->tbits;
+  u.tbits = c->tbits_local;
   u.kbits = c->kbits;
+  u.inst_toff = c->inst_toff;
   u.row_ptr = c->row_ptr;
   u.term = c->term;
   u.val32 = c->val32;
@@ -957,12 +1109,17 @@ ivf_status grow_means(ivf_ctx* c, int64_t new_cap) {
 // After an update step (means mcur -> mcur^1) whose new means did not fit
 // (STS_CAPACITY): grow and run the update again from the same assignment.
 // Synchronises.
-ivf_status redo_update_if_overflow(ivf_ctx* c, int src) {
+// heads_wanted (optional) receives the number of lists that qualified as
+// dense rows in the rebuilt inverted file, read in the same synchronisation.
+ivf_status redo_update_if_overflow(ivf_ctx* c, int src, long long* heads_wanted = nullptr) {
   for (int attempt = 0; attempt < 4; ++attempt) {
     unsigned st = 0;
     int64_t e_new = 0;
     CK(c, cudaMemcpyAsync(&st, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaMemcpyAsync(&e_new, c->mptr[c->mcur ^ 1] + c->Kt, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+    if (heads_wanted)
+      CK(c, cudaMemcpyAsync(heads_wanted, &c->dc->heads_wanted, sizeof(long long), cudaMemcpyDeviceToHost,
+                            c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (!(st & STS_CAPACITY)) return IVF_OK;
     CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), c->stream));
@@ -1221,10 +1378,12 @@ ivf_status ivf_update(ivf_ctx* c) {
     CK(c, timing_event(c, &e1));
     c->tcalls.push_back({1, e0});
   }
-  ST(redo_update_if_overflow(c, c->alatest));
+  long long wanted = 0;
+  ST(redo_update_if_overflow(c, c->alatest, &wanted));
   c->mcur ^= 1;
   c->iteration += 1;
   c->members_valid = true;
+  ST(grow_head_if_needed(c, wanted));
   return IVF_OK;
 }
 
@@ -1279,6 +1438,7 @@ ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_
     c->iteration += 1;
     c->members_valid = true;
     ++done;
+    ST(grow_head_if_needed(c, c->hc->heads_wanted));
     if (c->hc->status) ST(check_status(c));
     if (last_stats) fill_stats(c, last_stats);
     if (r >= 2 && c->hc->cnt[0] == 0) {

@@ -31,6 +31,12 @@ struct AssignArgs {
   int32_t n_inst;
   const int64_t* inst_docs;  // [n_inst+1]
   const int32_t* inst_clu;   // [n_inst+1]
+  // Optional subset of the instances (a batched context launches one kernel
+  // per class of instances): work item o belongs to listed instance q with
+  // obj_prefix[q] <= o < obj_prefix[q+1]; null = every object in order.
+  const int32_t* obj_inst;   // [n_obj_inst]
+  const int64_t* obj_prefix; // [n_obj_inst+1]
+  int32_t n_obj_inst;
   const int64_t* term_ptr;   // [D+1]
   const void* cid;           // [E] local cluster id & 0xFFFF (uint16), or int32 ids
   const void* w;             // [E] storage type
@@ -128,12 +134,13 @@ struct UpdateArgs {
   int32_t n_inst;
   int64_t kt;   // total clusters
   int64_t dt;   // total terms
-  int tbits, kbits;
+  int tbits, kbits;  // key bits: the largest instance's term count, the total cluster count
   const int64_t* row_ptr;
   const int32_t* term;
   const float* val32;
   const int64_t* inst_docs;
   const int32_t* inst_clu;
+  const int64_t* inst_toff;  // [n_inst+1] first global term id of each instance
   const int32_t* assign;  // local cluster ids
   int32_t empty_policy;
   // old and new cluster-major means
@@ -196,6 +203,7 @@ struct IvfBuildArgs {
   const int64_t* inst_toff;  // [n_inst+1] term offsets of the instances
   uint32_t* hflags;      // [Dt+1] scratch
   int64_t* d_heads;      // [1] receives the number of dense rows
+  int64_t* d_heads_wanted;  // [1] receives the number of lists that qualified (may exceed head_max)
   // scratch
   uint32_t* k32a;
   uint32_t* k32b;

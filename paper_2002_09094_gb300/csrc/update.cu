@@ -48,6 +48,19 @@ __device__ __forceinline__ int find_inst32(const int32_t* offs, int n_inst, int6
   return lo;
 }
 
+template <typename T>
+__device__ __forceinline__ int find_inst(const T* offs, int n_inst, T x) {
+  int lo = 0, hi = n_inst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (offs[mid] <= x)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ int find_inst64(const int64_t* offs, int n_inst, int64_t x) {
   int lo = 0, hi = n_inst - 1;
   while (lo < hi) {
@@ -102,9 +115,11 @@ __global__ void k_expand(UpdateArgs a) {
   for (int64_t i = gw; i < a.n_docs; i += nw) {
     const int b = a.n_inst > 1 ? find_inst64(a.inst_docs, a.n_inst, i) : 0;
     const uint64_t gc = (uint64_t)(a.inst_clu[b] + a.assign[i]);
+    // the instance's own term id: a cluster's terms all come from its instance
+    const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[b] : 0;
     const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
     for (int64_t h = r0 + lane; h < r1; h += 32) {
-      a.k64a[h] = (gc << a.tbits) | (uint64_t)(uint32_t)a.term[h];
+      a.k64a[h] = (gc << a.tbits) | (uint64_t)(uint32_t)(a.term[h] - t0);
       a.v32a[h] = __float_as_uint(a.val32[h]);
     }
   }
@@ -232,7 +247,8 @@ __global__ void k_write_entries(UpdateArgs a) {
     const double nrm = a.sum_norm[j];
     if (!(nrm > 0.0)) continue;
     const int64_t o = a.mptr_new[j] + (int64_t)(a.flags[u] - a.flags[a.uptr[j]]);
-    a.mterm_new[o] = (int32_t)(key & tmask);
+    const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)j)] : 0;
+    a.mterm_new[o] = (int32_t)(key & tmask) + t0;
     a.mval_new[o] = __ddiv_rn(s, nrm);
     a.mclu_new[o] = (int32_t)j;
     neg |= s < 0.0;
@@ -351,6 +367,7 @@ __global__ void k_head_slots(IvfBuildArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const int64_t tot = (int64_t)a.hflags[a.dt];
     *a.d_heads = tot < a.head_max ? tot : a.head_max;
+    if (a.d_heads_wanted) *a.d_heads_wanted = tot;
   }
 }
 

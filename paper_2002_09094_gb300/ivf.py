@@ -50,7 +50,8 @@ class Config(ctypes.Structure):
     _fields_ = [("n_docs", ctypes.c_int64), ("n_terms", ctypes.c_int64), ("nnz", ctypes.c_int64),
                 ("k", ctypes.c_int32), ("storage", ctypes.c_int32), ("rescore", ctypes.c_int32),
                 ("empty_policy", ctypes.c_int32), ("k_tile", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
-                ("flags", ctypes.c_uint32), ("means_capacity", ctypes.c_int32)]
+                ("flags", ctypes.c_uint32), ("means_capacity", ctypes.c_int32),
+                ("dense_head_bytes", ctypes.c_int64)]
 
 
 class IterStats(ctypes.Structure):
@@ -174,7 +175,7 @@ class IVF:
     def __init__(self, row_ptr, term, val, n_terms: int, k: int, storage: str = "f32", rescore: bool = True,
                  empty_policy: int = 0, k_tile: int = 0, warps_per_block: int = 0, validate: bool = False,
                  use_graph: bool = True, stream=None, kernel: str = "auto", means_capacity: int = 0,
-                 _batched=None):
+                 dense_head_bytes: int = 0, _batched=None):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p(0)
         rp, rk = _ptr(row_ptr, np.int64)
@@ -185,7 +186,8 @@ class IVF:
         flags = (IVF_FLAG_VALIDATE if validate else 0) | (0 if use_graph else IVF_FLAG_NO_GRAPH) | KERNEL_FLAGS[kernel]
         cfg = Config(n_docs=n_docs, n_terms=int(n_terms), nnz=nnz, k=int(k), storage=STORAGE[storage],
                      rescore=1 if rescore else 0, empty_policy=int(empty_policy), k_tile=int(k_tile),
-                     warps_per_block=int(warps_per_block), flags=flags, means_capacity=int(means_capacity))
+                     warps_per_block=int(warps_per_block), flags=flags, means_capacity=int(means_capacity),
+                     dense_head_bytes=int(dense_head_bytes))
         self.stream = _default_stream() if stream is None else stream
         if _batched is None:
             s = self._lib.ivf_create(ctypes.byref(cfg), rp, tp, vptr, ctypes.c_void_p(self.stream),

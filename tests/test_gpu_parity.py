@@ -616,3 +616,26 @@ def test_dense_head_wide_tiles_bit_equal(k):
     wide = max(out)
     for rep in lockstep(c, k, ids, 2, kernel="dense_head", k_tile=wide):
         assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_dense_head_rows_grow_on_demand(use_graph):
+    """A context that starts with room for a single dense row grows its rows
+    when more lists qualify (at the kernel choice and after updates) and ends
+    with exactly the results of a roomy context."""
+    c = corpus_for(4000, 4000, mean_len=35.0, seed=35)
+    k = 1500
+    ids = dg.init_doc_ids(c.n_docs, k, 35)
+    out = []
+    for budget in (0, 1024 * 4):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel="dense_head", k_tile=1024,
+                     use_graph=use_graph, dense_head_bytes=budget) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(3)
+            st = m.assign()
+            out.append((m.get_assign(), m.get_best(), m.get_gap(), st["entries_visited"],
+                        m.info()["dense_head_rows"]))
+    assert out[1][4] == out[0][4] > 1
+    for x, y in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    assert out[0][3] == out[1][3]
