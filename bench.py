@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--n-docs", type=int, default=0, help="use only this many documents of the workload "
                    "(same generator; for small profiling cases)")
     p.add_argument("--k", type=int, default=0, help="override the number of clusters (profiling cases)")
-    p.add_argument("--kernel", choices=["auto", "dense_head", "sparse"], default="auto",
+    p.add_argument("--kernel", choices=["auto", "dense_head", "sparse", "tensor_head"], default="auto",
                    help="assignment kernel family (auto = the autotuner picks)")
     p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -403,7 +403,8 @@ def run_ours(args, rank, world, local):
                       "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (CSR %.2f GB); no flush" % (c.nnz * 8 / 1e9),
                       "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"],
-                      "kernel": ("dense_head r=%d sub=%d theta=%.2f rows=%d" % (
+                      "kernel": ("%s r=%d sub=%d theta=%.2f rows=%d" % (
+                          "tensor_head" if info["dense_head_tensor"] else "dense_head",
                           info["dense_head_r"], info["dense_head_sub"], info["dense_head_theta"],
                           info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
                       "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},

@@ -63,11 +63,14 @@ typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
 /* ivf_config.flags */
 #define IVF_FLAG_VALIDATE 1u  /* check CSR rows (sorted, unique, in range, finite) at create/load */
 #define IVF_FLAG_NO_GRAPH 2u  /* ivf_iterate launches kernels directly instead of a CUDA graph */
-#define IVF_FLAG_DENSE_HEAD 4u  /* autotune only among dense-head kernels: posting lists that cover
+#define IVF_FLAG_DENSE_HEAD 4u  /* autotune only among CUDA-core dense-head kernels: posting lists that cover
                                    at least a fraction theta of the K clusters are also stored as
                                    dense rows (the paper's full inverted file, IFN, Section 4,
                                    for those terms only) and accumulated in registers */
 #define IVF_FLAG_SPARSE_ONLY 8u /* autotune only among kernels that read the sparse lists alone */
+#define IVF_FLAG_TENSOR_HEAD 16u /* FP16/BF16 storage: autotune only among dense-head kernels whose
+                                    head part is a tensor-core GEMM of the objects' dense head
+                                    values with the dense rows (cuBLAS), batch by batch */
 
 typedef struct {
   int64_t n_docs;      /* N >= 1 */
@@ -120,6 +123,7 @@ typedef struct {
   int64_t device_bytes;    /* device memory held by the context */
   int32_t dense_head_r;    /* 0: sparse kernel; else dense-head kernel with 32*r-cluster head tiles */
   int32_t dense_head_sub;  /* head tiles per shared-memory tile of the dense-head kernel */
+  int32_t dense_head_tensor; /* 1: the head part is computed by a tensor-core GEMM */
   float dense_head_theta;  /* lists covering >= theta * K clusters are stored densely */
   int64_t dense_head_rows; /* dense rows in the inverted file last built */
 } ivf_info;

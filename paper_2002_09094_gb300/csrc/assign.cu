@@ -90,12 +90,15 @@ struct ErrBound {
   __device__ __forceinline__ float e2(float rho_hat) const { return 2.f * (rel * fmaxf(rho_hat, 0.f) + abs); }
 };
 
-__device__ __forceinline__ ErrBound err_bound(int m, float nx, int storage, bool nonneg) {
+__device__ __forceinline__ ErrBound err_bound(int m, float nx, int storage, bool nonneg, bool tc_head) {
   const float u32 = 5.9604645e-08f;  // 2^-24
   const float fm = (float)m;
   // m + 1 roundings at most per rho_c: up to m FMAs in the head and tail
-  // chains together, plus the one addition that joins them
-  const float g = (fm + 1.f) * u32 / (1.f - (fm + 1.f) * u32);
+  // chains together, plus the one addition that joins them.  A head part
+  // summed by tensor cores is charged 2^-22 per addition (their FP32
+  // accumulation is not specified as round-to-nearest).
+  const float ua = tc_head ? 4.f * u32 : u32;
+  const float g = (fm + 1.f) * ua / (1.f - (fm + 1.f) * ua);
   float c, sub;
   if (storage == ST_F32) {
     c = u32;           // the mean's rounding to FP32; object values are exact
@@ -214,6 +217,8 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
   const IdT* __restrict__ cid = static_cast<const IdT*>(a.cid);
   const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
   const int32_t* __restrict__ head_slot = a.head_slot;
+  // (tensor-core head parts exist for 16-bit storage only)
+  const float* __restrict__ rho_tc = (R > 0 && sizeof(WT) == 2) ? a.rho_head : nullptr;
   constexpr int RR = R > 0 ? R : 1;
   constexpr int VEC = 16 / (int)sizeof(WT);      // values per 16-byte load of a dense head row
   constexpr int NG = RR >= VEC ? RR / VEC : 1;  // 16-byte groups per lane: clusters VEC*(32g + lane) + k
@@ -237,13 +242,13 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
       b = a.obj_inst[q];
       i = a.inst_docs[b] + (oi - a.obj_prefix[q]);
     } else {
-      i = oi;
+      i = a.obj_base + oi;
       b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
     }
     const int K = a.inst_clu[b + 1] - a.inst_clu[b];
     const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
     const int m = (int)(r1 - r0);
-    const ErrBound bound = err_bound(m, a.nx[i], a.storage, nonneg);
+    const ErrBound bound = err_bound(m, a.nx[i], a.storage, nonneg, a.rho_head != nullptr);
     const int tile = a.tiled ? a.k_tile : K;
     const int n_tiles = a.tiled ? (K + a.k_tile - 1) / a.k_tile : 1;
     float best = -INFINITY, second = -INFINITY;
@@ -436,12 +441,33 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
           const int ng_live = (scnt + VEC * 32 - 1) / (VEC * 32);  // 16-byte groups holding a cluster < scnt
 #pragma unroll
           for (int r = 0; r < RR; ++r) acc[r] = 0.f;
-          for (int64_t h0 = r0; h0 < r1; h0 += 32) {
-            const TermInfo ti0 = load_term(h0 + lane, tt, !split && tt == 0);
-            if (!split) my_entries += (unsigned long long)ti0.len;
-            head_rows(__ballot_sync(IVF_FULL_MASK, ti0.slot >= 0), ti0.slot, ti0.v, lo + sbase, ng_live);
-            if (!split)
-              tail_scatter(__ballot_sync(IVF_FULL_MASK, h0 + lane < r1 && ti0.slot < 0), ti0.beg, ti0.len, ti0.v);
+          if (!split || rho_tc == nullptr) {
+            for (int64_t h0 = r0; h0 < r1; h0 += 32) {
+              const TermInfo ti0 = load_term(h0 + lane, tt, !split && tt == 0);
+              if (!split) my_entries += (unsigned long long)ti0.len;
+              if (rho_tc == nullptr)
+                head_rows(__ballot_sync(IVF_FULL_MASK, ti0.slot >= 0), ti0.slot, ti0.v, lo + sbase, ng_live);
+              if (!split)
+                tail_scatter(__ballot_sync(IVF_FULL_MASK, h0 + lane < r1 && ti0.slot < 0), ti0.beg, ti0.len,
+                             ti0.v);
+            }
+          }
+          if (rho_tc != nullptr) {
+            // the head part from the tensor-core GEMM: same lane-to-cluster map
+            const float* __restrict__ rr = rho_tc + (i - a.obj_base) * a.rho_ld + lo + sbase;
+#pragma unroll
+            for (int g = 0; g < NG; ++g) {
+              if (g < ng_live) {
+#pragma unroll
+                for (int k4 = 0; k4 < VEC; k4 += 4) {
+                  const float4 h4 = __ldg(reinterpret_cast<const float4*>(rr + VEC * (32 * g + lane) + k4));
+                  acc[g * VEC + k4] = h4.x;
+                  acc[g * VEC + k4 + 1] = h4.y;
+                  acc[g * VEC + k4 + 2] = h4.z;
+                  acc[g * VEC + k4 + 3] = h4.w;
+                }
+              }
+            }
           }
           __syncwarp();
           float* rs = rho + sbase;

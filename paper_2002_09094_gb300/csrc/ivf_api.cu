@@ -13,6 +13,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cublas_v2.h>
+
 #include "../../include/ivf.h"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -54,6 +56,7 @@ struct Shape {
   int blocks = 0;
   int head_r = 0;     // registers per lane of the dense-head accumulator (0 = no dense head)
   int head_sub = 1;   // dense-head sub-tiles (32 * head_r clusters) per shared-memory tile
+  bool tc = false;    // head part by a tensor-core GEMM (16-bit storage, one instance)
   float head_theta = 0.f;  // a list covering at least this fraction of K is stored densely
 };
 
@@ -174,6 +177,15 @@ struct ivf_ctx {
   };
   std::vector<ClassPlan> cls;
   bool use_classes = false;
+  // tensor-core head: objects in batches of tc_batch; per batch the dense
+  // head values xh [tc_batch x head_max] (16-bit) and the GEMM result
+  // rho_h [tc_batch x kpad] (FP32)
+  cublasHandle_t blas = nullptr;
+  void* blas_ws = nullptr;
+  void* xh = nullptr;
+  float* rho_h = nullptr;
+  int64_t tc_batch = 0;
+  int64_t tc_alloc_rows = 0, tc_alloc_kpad = 0, tc_alloc_batch = 0;
   bool tuned = false;
   bool tuned_on_updated_means = false;  // the choice was made on means from an update step
   // state
@@ -553,6 +565,7 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
     a.inst_toff = c->inst_toff;
     a.hflags = c->hflags;
     a.d_heads = reinterpret_cast<int64_t*>(&c->dc->heads);
+    a.zero_rows = c->shape.tc ? c->head_max : 0;  // the GEMM reads every row
     a.d_heads_wanted = reinterpret_cast<int64_t*>(&c->dc->heads_wanted);
   }
   return a;
@@ -587,7 +600,8 @@ ivf_status alloc_head(ivf_ctx* c, int head_r) {
 // the current means; the lists that did not fit were read sparsely, which is
 // exact but slower.  Synchronises only when it grows.
 ivf_status grow_head_if_needed(ivf_ctx* c, long long wanted) {
-  if (c->shape.head_r <= 0 || !c->head_slot || wanted <= c->head_max) return IVF_OK;
+  // (the tensor-core head keeps its row count: the GEMM's depth is fixed)
+  if (c->shape.head_r <= 0 || c->shape.tc || !c->head_slot || wanted <= c->head_max) return IVF_OK;
   const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
   const int64_t cap_rows = std::max<int64_t>(1, kHeadMaxBytes / (c->kpad * vb));
   const int64_t rows = std::min<int64_t>({c->Dt, cap_rows, (int64_t)wanted + wanted / 4 + 64});
@@ -710,6 +724,50 @@ ivf_status ensure_toff(ivf_ctx* c, int k_tile) {
   return IVF_OK;
 }
 
+// Tensor-core head: a fixed number of dense rows (the GEMM depth), sized
+// from the lists that qualify now with a quarter of room, and the per-batch
+// buffers; lists beyond the rows are read sparsely (exact).
+ivf_status setup_tc(ivf_ctx* c, long long wanted) {
+  const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
+  const int64_t rows = std::min<int64_t>(c->Dt, std::max<int64_t>(64, ((wanted + wanted / 4) + 63) / 64 * 64));
+  if (rows != c->head_max) {
+    dfree(c, c->wd);
+    c->wd = nullptr;
+    char* p = nullptr;
+    ST(dalloc(c, &p, rows * c->kpad * vb));
+    c->wd = p;
+    c->head_max = rows;
+  }
+  // batches: GEMM output of at most ~3 GB, a multiple of 128 objects
+  c->tc_batch = std::min<int64_t>(c->N, std::max<int64_t>(8192, (int64_t(3) << 30) / (c->kpad * 4)) / 128 * 128);
+  if (c->tc_batch < 1) c->tc_batch = c->N;
+  if (!c->xh || c->tc_alloc_rows != rows || c->tc_alloc_batch != c->tc_batch || c->tc_alloc_kpad != c->kpad) {
+    dfree(c, c->xh);
+    dfree(c, c->rho_h);
+    c->xh = nullptr;
+    c->rho_h = nullptr;
+    char* x = nullptr;
+    ST(dalloc(c, &x, c->tc_batch * rows * 2));
+    c->xh = x;
+    ST(dalloc(c, &c->rho_h, c->tc_batch * c->kpad));
+    c->tc_alloc_rows = rows;
+    c->tc_alloc_batch = c->tc_batch;
+    c->tc_alloc_kpad = c->kpad;
+  }
+  if (!c->blas) {
+    if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasCreate failed");
+    char* ws = nullptr;
+    const int64_t ws_bytes = int64_t(32) << 20;
+    ST(dalloc(c, &ws, ws_bytes));
+    c->blas_ws = ws;
+    // a fixed workspace: no allocation inside the GEMM, so it can be captured in a graph
+    if (cublasSetWorkspace(c->blas, c->blas_ws, (size_t)ws_bytes) != CUBLAS_STATUS_SUCCESS)
+      return fail(c, IVF_E_CUDA, "cublasSetWorkspace failed");
+  }
+  if (cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasSetStream failed");
+  return IVF_OK;
+}
+
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
   c->shape = sh;
@@ -722,9 +780,45 @@ ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
     long long wanted = 0;
     CK(c, cudaMemcpyAsync(&wanted, &c->dc->heads_wanted, sizeof(long long), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    ST(grow_head_if_needed(c, wanted));
+    if (sh.tc) {
+      ST(setup_tc(c, wanted));
+      CK(c, launch_build_head(ivf_args(c, c->mcur), c->stream));  // rows cleared in full for the GEMM
+    } else {
+      ST(grow_head_if_needed(c, wanted));
+    }
   }
   drop_graphs(c);
+  return IVF_OK;
+}
+
+// One batch of the tensor-core head: dense head values of objects
+// [b0, b0 + nb), then rho_h = xh . wd (cuBLAS, FP32 accumulation): rho_h is
+// nb x kpad row-major, i.e. the column-major kpad x nb product of wd^T
+// (kpad x head_max, leading dimension kpad) and xh^T (head_max x nb).
+ivf_status enqueue_tc_gemm(ivf_ctx* c, int64_t b0, int64_t nb) {
+  CK(c, launch_build_xhead(b0, nb, c->row_ptr, c->term, c->val_store, c->head_slot, c->xh, c->head_max, c->stream));
+  const cudaDataType dt = c->cfg.storage == IVF_BF16 ? CUDA_R_16BF : CUDA_R_16F;
+  const float one = 1.f, zero = 0.f;
+  const cublasStatus_t st =
+      cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)c->kpad, (int)nb, (int)c->head_max, &one, c->wd, dt,
+                   (int)c->kpad, c->xh, dt, (int)c->head_max, &zero, c->rho_h, CUDA_R_32F, (int)c->kpad,
+                   CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+  if (st != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasGemmEx failed");
+  return IVF_OK;
+}
+
+// Assignment of objects [b0, b0 + nb) with the tensor-core head part.
+ivf_status enqueue_tc_batch(ivf_ctx* c, const Shape& sh, int target, int rescore, int64_t b0, int64_t nb,
+                            int64_t obj_stride) {
+  ST(enqueue_tc_gemm(c, b0, nb));
+  CK(c, cudaMemsetAsync(&c->dc->work, 0, sizeof(unsigned long long), c->stream));
+  AssignArgs a = assign_args(c, sh, target, rescore);
+  a.rho_head = c->rho_h;
+  a.rho_ld = c->kpad;
+  a.obj_base = b0;
+  a.obj_stride = (int32_t)obj_stride;
+  a.n_docs = (nb + obj_stride - 1) / obj_stride;
+  CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
   return IVF_OK;
 }
 
@@ -744,6 +838,23 @@ void set_class_objs(ivf_ctx* c, AssignArgs& a, int q) {
 // at least 65,536 objects), a sample that spans every instance.
 ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
   const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
+  if (sh.tc) {
+    // the first batch in full (the GEMM works on whole batches): time per object
+    const int64_t nb = std::min<int64_t>(c->tc_batch, c->N);
+    float ms_min = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), c->stream));
+      CK(c, cudaEventRecord(c->ev[0], c->stream));
+      ST(enqueue_tc_batch(c, sh, target, 0, 0, nb, 1));
+      CK(c, cudaEventRecord(c->ev[1], c->stream));
+      CK(c, cudaEventSynchronize(c->ev[1]));
+      float ms = 0.f;
+      CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+      ms_min = std::min(ms_min, ms);
+    }
+    *ms_out = ms_min / (float)nb;
+    return IVF_OK;
+  }
   AssignArgs a = assign_args(c, sh, target, 0);
   set_class_objs(c, a, q);
   const int64_t n = a.n_docs;
@@ -761,7 +872,7 @@ ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
     CK(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
     ms_min = std::min(ms_min, ms);
   }
-  *ms_out = ms_min;
+  *ms_out = ms_min / (float)a.n_docs;  // per object: comparable across sample sizes
   return IVF_OK;
 }
 
@@ -823,8 +934,19 @@ ivf_status autotune(ivf_ctx* c) {
     if (!ok) return fail(c, IVF_E_INVALID, "k_tile / warps_per_block not usable for this problem");
     cands.push_back(sh);
   } else {
-    const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0;
+    const bool tc_only = (c->cfg.flags & IVF_FLAG_TENSOR_HEAD) != 0;
+    const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0 || tc_only;
     const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0;
+    // tensor-core head: 16-bit storage, one instance, K over one 1,024-cluster tile
+    const bool tc_ok = !no_head && c->cfg.storage != IVF_F32 && c->n_inst == 1 && c->kmax > 32 * HEAD_R_LARGE;
+    if (tc_ok && (tc_only || !(c->cfg.flags & IVF_FLAG_DENSE_HEAD)))  // DENSE_HEAD: the CUDA-core head
+      for (int sub : {1, 2})
+        for (float theta : {0.5f, 0.25f, 0.125f})
+          if (shape_for(c, c->kmax, 0, 4, &sh, HEAD_R_LARGE, theta, sub)) {
+            sh.tc = true;
+            cands.push_back(sh);
+          }
+    if (tc_only && !tc_ok) return fail(c, IVF_E_UNSUPPORTED, "the tensor-core head needs FP16/BF16 storage, one instance and K > 1,024");
     if (!head_only) {
       if (shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
       for (int t : kTileChoices)
@@ -839,7 +961,7 @@ ivf_status autotune(ivf_ctx* c) {
       rs = {HEAD_R_SMALL};
     else
       rs = {HEAD_R_MID, HEAD_R_LARGE};
-    if (!no_head) {
+    if (!no_head && !tc_only) {
       for (int hr : rs)
         for (float theta : {0.5f, 0.25f})
           for (int wp : {8, 4}) {
@@ -861,9 +983,9 @@ ivf_status autotune(ivf_ctx* c) {
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
   // Contexts of the same shape in one process reuse the first choice, so
   // their FP32 rounding (which depends on the kernel family) is the same.
-  const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY));
+  const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY | IVF_FLAG_TENSOR_HEAD));
   auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
-                             (c->cfg.storage * 16 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
+                             (c->cfg.storage * 32 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
                              c->n_inst);
   const bool cacheable = c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0;
   {
@@ -935,6 +1057,9 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
       set_class_objs(c, a, (int)q);
       CK(c, launch_assign(a, sh.warps, sh.blocks, s, sh.head_r));
     }
+  } else if (c->shape.tc) {
+    for (int64_t b0 = 0; b0 < c->N; b0 += c->tc_batch)
+      ST(enqueue_tc_batch(c, c->shape, target, c->cfg.rescore, b0, std::min<int64_t>(c->tc_batch, c->N - b0), 1));
   } else {
     AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
     CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
@@ -1184,6 +1309,7 @@ void ivf_destroy(ivf_ctx* ctx) {
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : ctx->tev) cudaEventDestroy(ev);
+  if (ctx->blas) cublasDestroy(ctx->blas);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->hc) cudaFreeHost(ctx->hc);
   delete ctx;
@@ -1496,6 +1622,7 @@ ivf_status ivf_get_info(ivf_ctx* c, ivf_info* out) {
   out->device_bytes = c->bytes;
   out->dense_head_r = c->shape.head_r;
   out->dense_head_sub = c->shape.head_sub;
+  out->dense_head_tensor = c->shape.tc ? 1 : 0;
   out->dense_head_theta = c->shape.head_theta;
   long long heads = 0;
   if (c->shape.head_r > 0) {

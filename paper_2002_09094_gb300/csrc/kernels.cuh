@@ -69,6 +69,13 @@ struct AssignArgs {
   const void* wd;               // [T * kpad] storage type
   int64_t kpad;                 // row length, a multiple of the head sub-tile (32 * head_r)
   int32_t head_sub = 1;         // head sub-tiles of 32 * head_r clusters per shared-memory tile
+  // Tensor-core head (16-bit storage): the head part of rho for objects
+  // obj_base + o was computed beforehand by a GEMM of the objects' dense head
+  // values with the dense rows, rho_head[o * rho_ld + cluster] (FP32); the
+  // kernel reads it instead of walking the rows.
+  const float* rho_head;
+  int64_t rho_ld;
+  int64_t obj_base;
 };
 
 // Registers per lane of the head accumulator; the tile is 32 * R clusters.
@@ -203,6 +210,7 @@ struct IvfBuildArgs {
   const int64_t* inst_toff;  // [n_inst+1] term offsets of the instances
   uint32_t* hflags;      // [Dt+1] scratch
   int64_t* d_heads;      // [1] receives the number of dense rows
+  int64_t zero_rows;     // rows of wd cleared before filling (0: the rows in use)
   int64_t* d_heads_wanted;  // [1] receives the number of lists that qualified (may exceed head_max)
   // scratch
   uint32_t* k32a;
@@ -236,6 +244,11 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                    unsigned* status, unsigned* negative, cudaStream_t s);
 
 cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
+// Dense 16-bit head values of objects [i0, i0 + nb): x[(i - i0) * ldx + head_slot[t]] = val[h]
+// for every head term t of object i, zeros elsewhere.
+cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
+                               const void* val16, const int32_t* head_slot, void* x, int64_t ldx,
+                               cudaStream_t s);
 cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s);
 
 }  // namespace ivfk

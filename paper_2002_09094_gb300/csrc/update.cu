@@ -374,7 +374,7 @@ __global__ void k_head_slots(IvfBuildArgs a) {
 template <typename WT>
 __global__ void k_head_zero(IvfBuildArgs a) {
   WT* wd = static_cast<WT*>(a.wd);
-  const int64_t n = *a.d_heads * a.kpad;
+  const int64_t n = (a.zero_rows > 0 ? a.zero_rows : *a.d_heads) * a.kpad;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) wd[x] = from_f32<WT>(0.f);
 }
@@ -589,7 +589,7 @@ cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s) {
   IVF_CU(exclusive_scan_u32(a.hflags, a.hflags, a.dt, a.temp, s));
   k_head_slots<<<gD, T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
-  const unsigned gW = grid_for(a.head_max * a.kpad, T256, 16384);
+  const unsigned gW = grid_for((a.zero_rows > a.head_max ? a.zero_rows : a.head_max) * a.kpad, T256, 16384);
   const unsigned gF = grid_for(a.dt * 32, T256, 16384);
   switch (a.storage) {
     case ST_F16:
@@ -674,6 +674,32 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
 
 cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s) {
   k_check_row_ptr<<<grid_for(n, T256, 4096), T256, 0, s>>>(rp, n, nnz, status);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// Warp per object: scatter its head-term values into its dense row.
+__global__ void k_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
+                              const uint16_t* val16, const int32_t* head_slot, uint16_t* x, int64_t ldx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t o = gw; o < nb; o += nw) {
+    const int64_t i = i0 + o;
+    for (int64_t h = row_ptr[i] + lane; h < row_ptr[i + 1]; h += 32) {
+      const int32_t s = head_slot[term[h]];
+      if (s >= 0) x[o * ldx + s] = val16[h];
+    }
+  }
+}
+
+cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
+                               const void* val16, const int32_t* head_slot, void* x, int64_t ldx,
+                               cudaStream_t s) {
+  IVF_CU(cudaMemsetAsync(x, 0, sizeof(uint16_t) * nb * ldx, s));
+  k_build_xhead<<<grid_for(nb * 32, T256, 16384), T256, 0, s>>>(i0, nb, row_ptr, term,
+                                                                 static_cast<const uint16_t*>(val16), head_slot,
+                                                                 static_cast<uint16_t*>(x), ldx);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }

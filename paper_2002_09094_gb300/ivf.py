@@ -27,7 +27,9 @@ IVF_FLAG_VALIDATE = 1
 IVF_FLAG_NO_GRAPH = 2
 IVF_FLAG_DENSE_HEAD = 4
 IVF_FLAG_SPARSE_ONLY = 8
-KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG_SPARSE_ONLY}
+IVF_FLAG_TENSOR_HEAD = 16
+KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG_SPARSE_ONLY,
+                "tensor_head": IVF_FLAG_TENSOR_HEAD}
 
 # Every symbol include/ivf.h declares.
 EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_from_docs", "ivf_assign",
@@ -79,6 +81,7 @@ class Info(ctypes.Structure):
                 ("ivf_capacity", ctypes.c_int64), ("k_tile", ctypes.c_int32), ("warps_per_block", ctypes.c_int32),
                 ("iteration", ctypes.c_int32), ("storage", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("dense_head_r", ctypes.c_int32), ("dense_head_sub", ctypes.c_int32),
+                ("dense_head_tensor", ctypes.c_int32),
                 ("dense_head_theta", ctypes.c_float),
                 ("dense_head_rows", ctypes.c_int64)]
 

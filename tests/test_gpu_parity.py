@@ -639,3 +639,56 @@ def test_dense_head_rows_grow_on_demand(use_graph):
     for x, y in zip(out[0][:3], out[1][:3]):
         assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
     assert out[0][3] == out[1][3]
+
+
+# ----------------------------------------------------- tensor-core head
+
+
+@pytest.mark.parametrize("storage,tol", [("f16", 3e-3), ("bf16", 2.5e-2)])
+def test_tensor_head_lockstep(storage, tol):
+    """Head part from the tensor-core GEMM (16-bit operands, FP32
+    accumulation), tail and argmax by the CUDA-core kernel: assignments equal
+    the FP64 argmax at every iteration, the Eq. 15 count is exact."""
+    c = corpus_for(6000, 6000, mean_len=40.0, seed=37)
+    k = 2500
+    ids = dg.init_doc_ids(c.n_docs, k, 37)
+    reps = lockstep(c, k, ids, 3, storage=storage, best_tol=tol, kernel="tensor_head")
+    for rep in reps:
+        assert_report_ok(rep)
+
+
+def test_tensor_head_several_batches_equal_cuda_core_head():
+    """K = 30,000 makes the GEMM output of 40,000 objects span two batches;
+    the assignments equal those of the CUDA-core head (both are the FP64
+    argmax), sampled objects are checked against the oracle, and two runs
+    give identical bits."""
+    c = corpus_for(40000, 20000, mean_len=30.0, seed=38)
+    k = 30000
+    ids = dg.init_doc_ids(c.n_docs, k, 38)
+    out = {}
+    for kernel in ("tensor_head", "tensor_head", "dense_head"):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, storage="bf16", kernel=kernel) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(2)
+            st = m.assign()
+            inf = m.info()
+            res = (m.get_assign(), m.get_best(), m.get_gap(), st["entries_visited"], inf["dense_head_tensor"])
+        if kernel in out:
+            for x, y in zip(out[kernel][:3], res[:3]):
+                assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+        out[kernel] = res
+    assert out["tensor_head"][4] == 1 and out["dense_head"][4] == 0
+    assert np.array_equal(out["tensor_head"][0], out["dense_head"][0])
+    assert out["tensor_head"][3] == out["dense_head"][3]
+    rows = np.random.default_rng(38).choice(c.n_docs, 1500, replace=False)
+    for rep in lockstep(c, k, ids, 2, rows=rows, storage="bf16", best_tol=2.5e-2, kernel="tensor_head"):
+        assert_report_ok(rep, check_objective=False)
+
+
+def test_tensor_head_needs_16bit_storage():
+    c = corpus_for(3000, 3000, seed=39)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, 1500, kernel="tensor_head") as m:
+        m.set_means_from_docs(dg.init_doc_ids(c.n_docs, 1500, 39))
+        with pytest.raises(ivf.IvfError) as e:
+            m.assign()
+        assert e.value.status == ivf.IVF_E_UNSUPPORTED
