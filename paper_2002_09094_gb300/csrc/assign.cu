@@ -201,12 +201,14 @@ __device__ __forceinline__ void unpack16<__nv_bfloat16>(uint4 raw, float* e) {
 // the dense-head kernels hold 32R-cluster accumulators and two rows in
 // flight -- 96 for FP32 rows, 128 for 16-bit rows of the 1,024-cluster tile
 // (no spills; 96 would spill there).
-template <typename WT, int R>
+// TC: the head part comes from the tensor-core GEMM (a.rho_head), so no dense
+// rows are walked and the row registers are not needed (80 registers).
+template <typename WT, int R, bool TC>
 constexpr int assign_max_regs() {
-  return R == 0 ? 64 : (sizeof(WT) == 4 ? 96 : (R >= 32 ? 128 : 96));
+  return R == 0 ? 64 : (TC ? 80 : (sizeof(WT) == 4 ? 96 : (R >= 32 ? 128 : 96)));
 }
-template <typename WT, typename IdT, int R, bool SPLIT = false>
-__global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArgs a) {
+template <typename WT, typename IdT, int R, bool SPLIT = false, bool TC = false>
+__global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const AssignArgs a) {
   extern __shared__ __align__(16) float smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* rho = smem + (size_t)warp * (a.tile_cap + 2 * CAND_MAX);
@@ -218,7 +220,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
   const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
   const int32_t* __restrict__ head_slot = a.head_slot;
   // (tensor-core head parts exist for 16-bit storage only)
-  const float* __restrict__ rho_tc = (R > 0 && sizeof(WT) == 2) ? a.rho_head : nullptr;
+  const float* __restrict__ rho_tc = (R > 0 && TC) ? a.rho_head : nullptr;
   constexpr int RR = R > 0 ? R : 1;
   constexpr int VEC = 16 / (int)sizeof(WT);      // values per 16-byte load of a dense head row
   constexpr int NG = RR >= VEC ? RR / VEC : 1;  // 16-byte groups per lane: clusters VEC*(32g + lane) + k
@@ -445,7 +447,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R>())) k_assign(const AssignArg
             for (int64_t h0 = r0; h0 < r1; h0 += 32) {
               const TermInfo ti0 = load_term(h0 + lane, tt, !split && tt == 0);
               if (!split) my_entries += (unsigned long long)ti0.len;
-              if (rho_tc == nullptr)
+              if constexpr (!TC)
                 head_rows(__ballot_sync(IVF_FULL_MASK, ti0.slot >= 0), ti0.slot, ti0.v, lo + sbase, ng_live);
               if (!split)
                 tail_scatter(__ballot_sync(IVF_FULL_MASK, h0 + lane < r1 && ti0.slot < 0), ti0.beg, ti0.len,
@@ -706,7 +708,16 @@ __global__ void k_reduce_final(const ReduceArgs a, int nblocks) {
 }
 
 template <typename WT>
-const void* assign_fn_r(int head_r, int head_sub) {
+const void* assign_fn_r(int head_r, int head_sub, bool tc) {
+  if (tc) {
+    if constexpr (sizeof(WT) == 2) {
+      if (head_r != HEAD_R_LARGE) return nullptr;
+      return head_sub > 1 ? reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE, true, true>)
+                          : reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE, false, true>);
+    } else {
+      return nullptr;
+    }
+  }
   if (head_sub > 1)
     return head_r == HEAD_R_LARGE ? reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE, true>)
                                   : nullptr;
@@ -722,19 +733,28 @@ const void* assign_fn_r(int head_r, int head_sub) {
   }
 }
 
-const void* assign_fn_for(int storage, int head_r, int head_sub) {
+const void* assign_fn_for(int storage, int head_r, int head_sub, bool tc) {
   switch (storage) {
     case ST_F16:
-      return assign_fn_r<__half>(head_r, head_sub);
+      return assign_fn_r<__half>(head_r, head_sub, tc);
     case ST_BF16:
-      return assign_fn_r<__nv_bfloat16>(head_r, head_sub);
+      return assign_fn_r<__nv_bfloat16>(head_r, head_sub, tc);
     default:
-      return assign_fn_r<float>(head_r, head_sub);
+      return assign_fn_r<float>(head_r, head_sub, tc);
   }
 }
 
 template <typename WT>
 void launch_typed(const AssignArgs& a, int warps, int blocks, size_t smem, cudaStream_t s, int head_r) {
+  if constexpr (sizeof(WT) == 2) {
+    if (a.rho_head != nullptr) {  // tensor-core head (head_r == HEAD_R_LARGE, checked by the caller)
+      if (a.head_sub > 1)
+        k_assign<WT, uint16_t, HEAD_R_LARGE, true, true><<<blocks, warps * 32, smem, s>>>(a);
+      else
+        k_assign<WT, uint16_t, HEAD_R_LARGE, false, true><<<blocks, warps * 32, smem, s>>>(a);
+      return;
+    }
+  }
   if (head_r == HEAD_R_LARGE && a.head_sub > 1) {
     k_assign<WT, uint16_t, HEAD_R_LARGE, true><<<blocks, warps * 32, smem, s>>>(a);
     return;
@@ -763,11 +783,11 @@ size_t assign_smem_bytes(int tile_cap, int warps) {
 
 // The shared-memory opt-in of a kernel is process-wide, so it only ever grows:
 // a context with a smaller tile must not lower it under another's launches.
-cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r, int head_sub) {
+cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r, int head_sub, bool tc) {
   static std::mutex mu;
   static std::map<const void*, size_t> raised;
   const size_t bytes = assign_smem_bytes(tile_cap, warps);
-  const void* fn = assign_fn_for(storage, head_r, head_sub);
+  const void* fn = assign_fn_for(storage, head_r, head_sub, tc);
   if (fn == nullptr) return cudaErrorInvalidValue;
   std::lock_guard<std::mutex> lk(mu);
   size_t& cur = raised[fn];
@@ -777,10 +797,10 @@ cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r, int
   return e;
 }
 
-int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r, int head_sub) {
+int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r, int head_sub, bool tc) {
   int nb = 0;
-  if (assign_prepare(storage, tile_cap, warps, head_r, head_sub) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage, head_r, head_sub), warps * 32,
+  if (assign_prepare(storage, tile_cap, warps, head_r, head_sub, tc) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, assign_fn_for(storage, head_r, head_sub, tc), warps * 32,
                                                     assign_smem_bytes(tile_cap, warps)) != cudaSuccess)
     return 0;
   return nb;
@@ -788,7 +808,8 @@ int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r, i
 
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r) {
   if ((a.tiled && a.toff == nullptr) || (head_r > 0 && (a.head_slot == nullptr || a.wd == nullptr)) ||
-      a.head_sub < 1 || (a.head_sub > 1 && head_r != HEAD_R_LARGE))
+      a.head_sub < 1 || (a.head_sub > 1 && head_r != HEAD_R_LARGE) ||
+      (a.rho_head != nullptr && (head_r != HEAD_R_LARGE || a.storage == ST_F32)))
     return cudaErrorInvalidValue;
   const size_t smem = assign_smem_bytes(a.tile_cap, warps);
   switch (a.storage) {

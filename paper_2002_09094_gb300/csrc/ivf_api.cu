@@ -673,7 +673,7 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
 // head_r > 0 selects the dense-head kernel, whose shared-memory tile is
 // head_sub sub-tiles of 32 * head_r clusters.
 bool shape_for(ivf_ctx* c, int32_t kmax, int k_tile, int warps_req, Shape* out, int head_r = 0, float theta = 0.f,
-               int head_sub = 1) {
+               int head_sub = 1, bool tc = false) {
   Shape sh;
   if (head_r > 0) {
     if (head_sub < 1 || !is_pow2(head_sub)) return false;
@@ -703,7 +703,8 @@ bool shape_for(ivf_ctx* c, int32_t kmax, int k_tile, int warps_req, Shape* out, 
   int warps = warps_req > 0 ? std::min(warps_req, wmax) : std::min(wmax, 8);
   if (warps_req > 0 && (size_t)warps_req * per_warp > kSmemBudget) return false;
   sh.warps = warps;
-  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps, head_r, sh.head_sub);
+  sh.tc = tc;
+  int bps = assign_max_blocks_per_sm(c->cfg.storage, sh.tile_cap, warps, head_r, sh.head_sub, tc);
   if (bps < 1) return false;
   sh.blocks = bps * c->num_sms;
   *out = sh;
@@ -771,7 +772,7 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
   c->shape = sh;
-  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r, sh.head_sub));
+  CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r, sh.head_sub, sh.tc));
   if (sh.head_r > 0) ST(alloc_head(c, sh.head_r));
   IvfBuildArgs a = ivf_args(c, c->mcur);
   if (sh.tiled) CK(c, launch_build_toff(a, c->stream));
@@ -942,10 +943,8 @@ ivf_status autotune(ivf_ctx* c) {
     if (tc_ok && (tc_only || !(c->cfg.flags & IVF_FLAG_DENSE_HEAD)))  // DENSE_HEAD: the CUDA-core head
       for (int sub : {1, 2})
         for (float theta : {0.5f, 0.25f, 0.125f})
-          if (shape_for(c, c->kmax, 0, 4, &sh, HEAD_R_LARGE, theta, sub)) {
-            sh.tc = true;
-            cands.push_back(sh);
-          }
+          for (int wp : {4, 8})
+            if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_LARGE, theta, sub, true)) cands.push_back(sh);
     if (tc_only && !tc_ok) return fail(c, IVF_E_UNSUPPORTED, "the tensor-core head needs FP16/BF16 storage, one instance and K > 1,024");
     if (!head_only) {
       if (shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh)) cands.push_back(sh);
