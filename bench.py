@@ -392,12 +392,13 @@ def run_ours(args, rank, world, local):
     achieved = b_assign / (kern_ms / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(w.name, args.storage),
-            "kernel": "k_assign", "peak_source": f"{peak_kind} hbm_gbs",
+            "kernel": ("assign step: k_build_xhead + cuBLAS GEMM + k_assign" if info["dense_head_tensor"]
+                       else "k_assign"), "peak_source": f"{peak_kind} hbm_gbs",
             "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
             "kernel_ms": round(kern_ms, 4)}
     out = {"metric": METRIC, "value": ms_per_step / 1e3 / world, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
            "data": "synthetic", "impl": "ours",
            "config": {"workload": w.name, "n_docs": c.n_docs, "n_terms": c.n_terms, "nnz": c.nnz, "k": w.k,
                       "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",

@@ -205,7 +205,7 @@ __device__ __forceinline__ void unpack16<__nv_bfloat16>(uint4 raw, float* e) {
 // rows are walked and the row registers are not needed (80 registers).
 template <typename WT, int R, bool TC>
 constexpr int assign_max_regs() {
-  return R == 0 ? 64 : (TC ? 80 : (sizeof(WT) == 4 ? 96 : (R >= 32 ? 128 : 96)));
+  return R == 0 ? 64 : (TC ? 80 : (sizeof(WT) == 4 ? (R >= 32 ? 96 : 72) : (R >= 32 ? 128 : 96)));
 }
 template <typename WT, typename IdT, int R, bool SPLIT = false, bool TC = false>
 __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const AssignArgs a) {
@@ -720,6 +720,7 @@ const void* assign_fn_r(int head_r, int head_sub, bool tc) {
   }
   if (head_sub > 1)
     return head_r == HEAD_R_LARGE ? reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_LARGE, true>)
+           : head_r == HEAD_R_MID ? reinterpret_cast<const void*>(&k_assign<WT, uint16_t, HEAD_R_MID, true>)
                                   : nullptr;
   switch (head_r) {
     case HEAD_R_SMALL:
@@ -757,6 +758,10 @@ void launch_typed(const AssignArgs& a, int warps, int blocks, size_t smem, cudaS
   }
   if (head_r == HEAD_R_LARGE && a.head_sub > 1) {
     k_assign<WT, uint16_t, HEAD_R_LARGE, true><<<blocks, warps * 32, smem, s>>>(a);
+    return;
+  }
+  if (head_r == HEAD_R_MID && a.head_sub > 1) {
+    k_assign<WT, uint16_t, HEAD_R_MID, true><<<blocks, warps * 32, smem, s>>>(a);
     return;
   }
   switch (head_r) {
@@ -808,7 +813,7 @@ int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r, i
 
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r) {
   if ((a.tiled && a.toff == nullptr) || (head_r > 0 && (a.head_slot == nullptr || a.wd == nullptr)) ||
-      a.head_sub < 1 || (a.head_sub > 1 && head_r != HEAD_R_LARGE) ||
+      a.head_sub < 1 || (a.head_sub > 1 && head_r != HEAD_R_LARGE && head_r != HEAD_R_MID) ||
       (a.rho_head != nullptr && (head_r != HEAD_R_LARGE || a.storage == ST_F32)))
     return cudaErrorInvalidValue;
   const size_t smem = assign_smem_bytes(a.tile_cap, warps);

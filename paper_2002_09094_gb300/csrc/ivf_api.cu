@@ -977,6 +977,13 @@ ivf_status autotune(ivf_ctx* c) {
             if (theta < 0.25f && wp != 4) continue;
             if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_LARGE, theta, sub)) cands.push_back(sh);
           }
+      // 512-cluster register tiles under a 2,048-cluster shared-memory tile:
+      // fewer registers (more resident warps) for more passes over the rows
+      for (float theta : {0.25f, 0.125f})
+        for (int wp : {4, 8}) {
+          if (c->cfg.warps_per_block > 0 && wp != c->cfg.warps_per_block) continue;
+          if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_MID, theta, 4)) cands.push_back(sh);
+        }
     }
   }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");

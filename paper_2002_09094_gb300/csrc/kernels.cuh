@@ -86,7 +86,7 @@ constexpr int HEAD_MAX_WARPS = 8;  // warps per block of the dense-head kernels
 
 size_t assign_smem_bytes(int tile_cap, int warps);
 cudaError_t assign_prepare(int storage, int tile_cap, int warps, int head_r = 0, int head_sub = 1, bool tc = false);
-// head_sub > 1 (split dense-head kernel) is available for head_r == HEAD_R_LARGE only.
+// head_sub > 1 (split dense-head kernel) is available for head_r == HEAD_R_LARGE and HEAD_R_MID.
 cudaError_t launch_assign(const AssignArgs& a, int warps, int blocks, cudaStream_t s, int head_r = 0);
 int assign_max_blocks_per_sm(int storage, int tile_cap, int warps, int head_r = 0, int head_sub = 1,
                              bool tc = false);
