@@ -573,7 +573,9 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
 
 // Buffers of the dense head rows for tiles of 32 * head_r clusters.
 ivf_status alloc_head(ivf_ctx* c, int head_r) {
-  const int64_t tile = 32 * (int64_t)head_r;
+  // batched contexts: rows padded to 1,024 clusters, so every class may use
+  // any register tile with the rows built for the largest class
+  const int64_t tile = 32 * (int64_t)(c->n_inst > 1 ? HEAD_R_LARGE : head_r);
   const int64_t kpad = ceil_div(c->kmax, tile) * tile;
   if (c->head_slot && c->kpad == kpad) return IVF_OK;
   dfree(c, c->head_slot);
@@ -879,7 +881,7 @@ ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
 
 // Kernels for the classes below the last one: untiled (their K fits one
 // tile), the sparse kernel or a dense-head kernel reading the rows built for
-// the main shape (same theta, register tile no wider than the main one's).
+// the main shape (same theta; the rows are padded to 1,024 clusters).
 ivf_status tune_classes(ivf_ctx* c) {
   for (size_t q = 0; q + 1 < c->cls.size(); ++q) {
     ivf_ctx::ClassPlan& p = c->cls[q];
@@ -891,7 +893,7 @@ ivf_status tune_classes(ivf_ctx* c) {
     if (!no_head)
       for (int hr : {HEAD_R_SMALL, HEAD_R_MID, HEAD_R_LARGE})
         for (int wp : {8, 4}) {
-          if (hr > c->shape.head_r) continue;
+          if (c->kpad % (32 * hr) != 0) continue;
           if (shape_for(c, p.kmax, 0, wp, &sh, hr, c->shape.head_theta) && !sh.tiled) cands.push_back(sh);
         }
     if (cands.empty()) cands.push_back(c->shape);  // cannot happen for K <= 1,024; kept for safety
