@@ -137,10 +137,13 @@ def test_batched_equals_single_instances():
         assert np.array_equal(mv[lo:hi], sv)
 
 
-@pytest.mark.parametrize("kernel", ["sparse", "dense_head"])
-def test_batched_lockstep_against_oracle(kernel):
-    ws = dg.batched_workloads(n_instances=4, n_range=(800, 2000), k_range=(8, 1500), d_range=(2000, 5000),
-                              nnz_range=(15.0, 50.0), iterations=3, seed=77)
+@pytest.mark.parametrize("kernel,seed,n_inst", [("sparse", 77, 4), ("dense_head", 77, 4), ("auto", 85, 5),
+                                                ("dense_head", 88, 5)])
+def test_batched_lockstep_against_oracle(kernel, seed, n_inst):
+    """Seed 77: K in two of the classes the batched assignment launches
+    separately (<= 1,024 and larger); seeds 85 and 88: all three classes."""
+    ws = dg.batched_workloads(n_instances=n_inst, n_range=(800, 2000), k_range=(8, 1600 if n_inst == 5 else 1500),
+                              d_range=(2000, 5000), nnz_range=(15.0, 50.0), iterations=3, seed=seed)
     cs = [dg.make_corpus(w.corpus) for w in ws]
     ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
     inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
@@ -503,8 +506,9 @@ def _signed(c, frac, seed):
     return dg.Corpus(c.row_ptr, c.term, val, c.n_terms)
 
 
-@pytest.mark.parametrize("kernel", ["sparse", "dense_head"])
-@pytest.mark.parametrize("storage,tol", [("f32", 1e-5), ("bf16", 2.5e-2)])
+@pytest.mark.parametrize("kernel,storage,tol", [("sparse", "f32", 1e-5), ("sparse", "bf16", 2.5e-2),
+                                                ("dense_head", "f32", 1e-5), ("dense_head", "bf16", 2.5e-2),
+                                                ("tensor_head", "bf16", 2.5e-2)])
 def test_mixed_sign_objects_lockstep(kernel, storage, tol):
     """Values of both signs: similarities can be negative, so unvisited
     clusters (similarity 0) compete for the argmax, and the error bound of the
