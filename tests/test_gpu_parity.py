@@ -405,6 +405,63 @@ def test_scale_workload_sampled_lockstep():
         assert_report_ok(rep, check_objective=False)
 
 
+def test_scale_workload_bf16_sampled_lockstep():
+    """The mixed-precision bench configuration (BF16 storage; after the first
+    update the autotuner picks the tensor-core head there) at full size:
+    sampled objects and every flagged near-tie equal the FP64 argmax, the
+    FP64 master means equal the oracle's update, Eq. 15 exact."""
+    w = dg.SCALE
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    rows = np.random.default_rng(321).choice(c.n_docs, 2000, replace=False)
+    reps = lockstep(c, w.k, ids, 2, rows=rows, storage="bf16", best_tol=2.5e-2)
+    for rep in reps:
+        assert_report_ok(rep, check_objective=False)
+
+
+def test_large_workload_full_size_sampled():
+    """8,000,000 docs x 2,000,000 terms, K = 80,000 in the benchmark's launch
+    configuration: 500 sampled objects equal the FP64 argmax at the first
+    assignment and, against the GPU's own FP64 means, at the second; 16
+    sampled non-empty clusters of the update equal the oracle's member sums
+    normalised; Eq. 15 exact at the first assignment."""
+    w = dg.LARGE
+    c = dg.make_corpus(w.corpus)
+    ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
+    rng = np.random.default_rng(808)
+    rows = rng.choice(c.n_docs, 500, replace=False)
+    m0 = sk.initial_means(c, ids)
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k) as m:
+        m.set_means_from_docs(ids)
+        st = m.assign()
+        a1, b1 = m.get_assign(), m.get_best()
+        rep = sk.lockstep_check(c, m0, a1, b1, rows=np.unique(np.concatenate([rows, np.flatnonzero(m.get_gap() <= 1e-3)[:500]])))
+        assert rep["mismatches"] == 0 and rep["best_ok"], (rep["mismatches"], rep["max_best_err"])
+        assert st["entries_visited"] == sk.multiplication_count(c, m0)
+        m.update()
+        gp, gt, gv = m.get_means()
+        # sampled clusters: the oracle's update restricted to their members
+        sizes = np.bincount(a1, minlength=w.k)
+        picks = rng.choice(np.flatnonzero(sizes > 0), 16, replace=False)
+        members = np.flatnonzero(np.isin(a1, picks))
+        sub_ptr = np.concatenate([[0], np.cumsum(np.diff(c.row_ptr)[members])]).astype(np.int64)
+        sel = np.concatenate([np.arange(c.row_ptr[i], c.row_ptr[i + 1]) for i in members])
+        sub = dg.Corpus(sub_ptr, c.term[sel], c.val[sel], c.n_terms)
+        new, _, _ = sk.update(sub, a1[members], m0)
+        for j in picks:
+            t_o, v_o = new.row(int(j))
+            t_g, v_g = gt[gp[j]:gp[j + 1]], gv[gp[j]:gp[j + 1]]
+            assert np.array_equal(t_o, t_g)
+            assert np.max(np.abs(v_o - v_g)) <= 1e-12
+        # second assignment (the tuned kernel) against the GPU's FP64 means
+        st2 = m.assign()
+        a2, b2 = m.get_assign(), m.get_best()
+        gm = sk.Means(ptr=gp, term=gt.astype(np.int64), val=gv, n_terms=c.n_terms)
+        rep2 = sk.lockstep_check(c, gm, a2, b2, rows=rows)
+        assert rep2["mismatches"] == 0 and rep2["best_ok"], (rep2["mismatches"], rep2["max_best_err"])
+        assert st2["n_changed"] > 0
+
+
 def test_large_k_tiled_sampled_lockstep():
     """K = 80,000 (> 65,536: tiled accumulator and 16-bit tile-local ids) on
     200,000 docs x 2,000,000 terms, lognormal(80) lengths, Zipf 1.0."""
