@@ -382,6 +382,20 @@ def run_ours(args, rank, world, local):
         means_np = m.get_means()
         assign_np = m.get_assign()
         m.close()
+        # mixed precision is compared with FP32 at equal assignments: the
+        # same number of iterations from the same initial means in FP32
+        equal_f32 = None
+        if args.storage != "f32":
+            cycles = args.warmup + args.steps + args.e2e_steps
+            with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage="f32",
+                         stream=stream.cuda_stream) as m32:
+                m32.set_means_from_docs(ids)
+                for q in range(cycles):
+                    m32.assign(stats=False)
+                    if q + 1 < cycles:
+                        m32.update()
+                a32 = m32.get_assign()
+            equal_f32 = {"iterations": cycles, "objects_differing": int(np.count_nonzero(a32 != assign_np))}
 
     ms_per_step = total_ms / args.steps
     n_steps = max(1, timing["n_assign"])
@@ -418,6 +432,8 @@ def run_ours(args, rank, world, local):
            "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)},
            "gpu_launches": int(launches), "clocks": clk}
+    if equal_f32 is not None:
+        out["assignments_vs_f32"] = equal_f32
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle.spherical_kmeans as sk
 
