@@ -140,7 +140,10 @@ ivf_status ivf_create(const ivf_config* cfg, const int64_t* row_ptr, const int32
 
 /* Replace the object values and terms (same N and nnz as at create time):
  * the host->device copy of a new batch of objects.  Row structure may
- * change.  Means and assignments are kept. */
+ * change.  Means and assignments are kept.  row_ptr is checked on the device
+ * (starts at 0, ends at nnz, non-decreasing) before anything changes, which
+ * synchronises once; on IVF_E_INVALID the previous objects stay in place.
+ * With IVF_FLAG_VALIDATE the rows are also checked as at create time. */
 ivf_status ivf_load_objects(ivf_ctx* ctx, const int64_t* row_ptr, const int32_t* term,
                             const float* val);
 
@@ -214,7 +217,9 @@ void ivf_destroy(ivf_ctx* ctx);
 typedef struct {
   int32_t n_assign;         /* ivf_assign calls in the window */
   int32_t n_update;         /* ivf_update calls in the window */
-  double assign_kernel_ms;  /* sum: the assignment kernel alone */
+  double assign_kernel_ms;  /* sum: the assignment kernel alone (with the tensor-core head:
+                               the dense head values, the GEMM and the kernel, batch by batch;
+                               with a batched context: the launches of every class) */
   double assign_step_ms;    /* sum: assignment kernel + FP64 re-score + reductions */
   double update_ms;         /* sum: update step including the inverted-file rebuild */
   int64_t entries_visited;  /* sum of the Eq. 15 multiplication counts */
@@ -225,16 +230,18 @@ ivf_status ivf_timing_reset(ivf_ctx* ctx, int32_t enable);
 /* Sums over the window so far; synchronises the stream. */
 ivf_status ivf_get_timing(ivf_ctx* ctx, ivf_timing* out);
 
-/* Number of kernels this library has launched in the process so far. */
+/* Number of kernels this library has launched in the process so far (its
+ * own kernels; the cuBLAS GEMM of the tensor-core head is not counted). */
 int64_t ivf_launch_count(void);
 /* Library version string. */
 const char* ivf_version(void);
 
 /* ------------------------------------------------------------------------
  * Batched form: many independent clustering problems of uneven N, K and D
- * in one context.  Every launch (assignment, re-score, update) covers all
- * instances at once; each instance's result is identical to running it
- * alone, because no arithmetic mixes instances.
+ * in one context.  Every launch (re-score, update) covers all instances at
+ * once, and the assignment one launch per class of instances by K (<= 512,
+ * <= 1,024, larger), each with its own autotuned kernel; no arithmetic mixes
+ * instances.
  * inst_docs int64[n_inst+1]: object offsets (row_ptr is the concatenation of
  *   the instances' CSR rows, term ids local to the instance);
  * inst_terms int32[n_inst]: D of each instance; inst_k int32[n_inst]: K.

@@ -1,7 +1,8 @@
 // C ABI of libivfkm (include/ivf.h): context, device layout, autotuner,
 // CUDA-graph iterations.  All arithmetic of the method runs in the kernels of
-// assign.cu, update.cu and radix.cu; this file validates, allocates, copies
-// and launches.
+// assign.cu, update.cu and radix.cu, plus (FP16/BF16 storage only) the cuBLAS
+// GEMM of the tensor-core head; this file validates, allocates, copies and
+// launches.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

@@ -244,7 +244,6 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                    const int64_t* inst_toff, const int32_t* inst_terms, int validate,
                                    unsigned* status, unsigned* negative, cudaStream_t s);
 
-cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s);
 // Dense 16-bit head values of objects [i0, i0 + nb): x[(i - i0) * ldx + head_slot[t]] = val[h]
 // for every head term t of object i, zeros elsewhere.
 cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,

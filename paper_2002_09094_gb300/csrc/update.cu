@@ -36,32 +36,8 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 1 << 20) {
   return (unsigned)g;
 }
 
-__device__ __forceinline__ int find_inst32(const int32_t* offs, int n_inst, int64_t x) {
-  int lo = 0, hi = n_inst - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if ((int64_t)offs[mid] <= x)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 template <typename T>
 __device__ __forceinline__ int find_inst(const T* offs, int n_inst, T x) {
-  int lo = 0, hi = n_inst - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (offs[mid] <= x)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int find_inst64(const int64_t* offs, int n_inst, int64_t x) {
   int lo = 0, hi = n_inst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -91,7 +67,7 @@ __device__ __forceinline__ int64_t lower_bound_dev(const K* a, int64_t n, K x) {
 __global__ void k_member_keys(UpdateArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_docs; i += stride) {
-    const int b = a.n_inst > 1 ? find_inst64(a.inst_docs, a.n_inst, i) : 0;
+    const int b = a.n_inst > 1 ? find_inst<int64_t>(a.inst_docs, a.n_inst, i) : 0;
     a.v32a[i] = (uint32_t)i;
     reinterpret_cast<uint32_t*>(a.k64a)[i] = (uint32_t)(a.inst_clu[b] + a.assign[i]);
   }
@@ -113,7 +89,7 @@ __global__ void k_expand(UpdateArgs a) {
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < a.n_docs; i += nw) {
-    const int b = a.n_inst > 1 ? find_inst64(a.inst_docs, a.n_inst, i) : 0;
+    const int b = a.n_inst > 1 ? find_inst<int64_t>(a.inst_docs, a.n_inst, i) : 0;
     const uint64_t gc = (uint64_t)(a.inst_clu[b] + a.assign[i]);
     // the instance's own term id: a cluster's terms all come from its instance
     const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[b] : 0;
@@ -307,7 +283,7 @@ __global__ void k_ivf_fill(IvfBuildArgs a, const uint32_t* perm) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
     const uint32_t e = perm[q];
     const int32_t gc = a.mclu[e];
-    const int b = a.n_inst > 1 ? find_inst32(a.inst_clu, a.n_inst, gc) : 0;
+    const int b = a.n_inst > 1 ? find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc) : 0;
     const int32_t local = gc - a.inst_clu[b];
     a.cid32[q] = local;
     a.cid16[q] = (uint16_t)(local & 0xFFFF);
@@ -348,7 +324,7 @@ __global__ void k_head_flags(IvfBuildArgs a) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.dt; p += stride) {
     int64_t min_nc = a.head_min_nc;
     if (a.n_inst > 1) {  // theta * K of the term's own instance
-      const int b = find_inst64(a.inst_toff, a.n_inst, p);
+      const int b = find_inst<int64_t>(a.inst_toff, a.n_inst, p);
       const int64_t kb = a.inst_clu[b + 1] - a.inst_clu[b];
       min_nc = (int64_t)ceilf(a.head_theta * (float)kb);
       if (min_nc < 1) min_nc = 1;
@@ -459,7 +435,7 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = gw; i < n_docs; i += nw) {
-    const int b = n_inst > 1 ? find_inst64(inst_docs, n_inst, i) : 0;
+    const int b = n_inst > 1 ? find_inst<int64_t>(inst_docs, n_inst, i) : 0;
     const int64_t toff = inst_toff[b];
     const int32_t d_local = inst_terms[b];
     const int64_t r0 = row_ptr[i], r1 = row_ptr[i + 1];
@@ -500,11 +476,6 @@ __global__ void k_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsig
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) bad |= rp[i + 1] < rp[i];
   if (blockIdx.x == 0 && threadIdx.x == 0) bad |= rp[0] != 0 || rp[n] != nnz;
   if (bad) atomicOr(status, (unsigned)STS_BAD_ROWS);
-}
-
-__global__ void k_fill_i64(int64_t* p, int64_t n, int64_t v) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = v;
 }
 
 }  // namespace
@@ -700,12 +671,6 @@ cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, c
   k_build_xhead<<<grid_for(nb * 32, T256, 16384), T256, 0, s>>>(i0, nb, row_ptr, term,
                                                                  static_cast<const uint16_t*>(val16), head_slot,
                                                                  static_cast<uint16_t*>(x), ldx);
-  IVF_LAUNCH_CHECK();
-  return cudaSuccess;
-}
-
-cudaError_t launch_fill_i64(int64_t* p, int64_t n, int64_t v, cudaStream_t s) {
-  k_fill_i64<<<grid_for(n, T256, 4096), T256, 0, s>>>(p, n, v);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }

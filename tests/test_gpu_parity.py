@@ -650,13 +650,18 @@ def test_load_objects_rejects_bad_row_ptr_and_stays_usable():
         assert np.array_equal(m.get_assign(), a0)
 
 
-@pytest.mark.parametrize("k", [1500, 4500])
-def test_dense_head_wide_tiles_bit_equal(k):
+@pytest.mark.parametrize("k,kind", [(1500, "poisson"), (4500, "poisson"), (3000, "lognormal")])
+def test_dense_head_wide_tiles_bit_equal(k, kind):
     """Shared-memory tiles of 1, 2 and 4 head sub-tiles (the sparse lists
     scattered once per wide tile, the dense rows per 1,024-cluster sub-tile)
     sum every rho_c in the same order, so their results are identical; K =
-    1,500 with a 2,048 tile runs untiled, K = 4,500 ends in a ragged tile."""
-    c = corpus_for(5000, 5000, mean_len=40.0, seed=k + 7)
+    1,500 with a 2,048 tile runs untiled, K = 4,500 ends in a ragged tile, the
+    lognormal lengths reach 400 terms (13 chunks of 32)."""
+    if kind == "lognormal":
+        c = corpus_for(5000, 5000, mean_len=90.0, seed=k + 7, kind="lognormal", lo=5, hi=400)
+        assert np.diff(c.row_ptr).max() > 128
+    else:
+        c = corpus_for(5000, 5000, mean_len=40.0, seed=k + 7)
     ids = dg.init_doc_ids(c.n_docs, k, k + 7)
     out = {}
     for kt in (1024, 2048, 4096):
