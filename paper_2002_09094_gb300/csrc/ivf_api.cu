@@ -96,6 +96,7 @@ struct ivf_ctx {
   std::vector<int32_t> h_inst_clu, h_inst_terms;
   // allocations
   std::vector<void*> allocs;
+  std::vector<int64_t> alloc_bytes;  // size of each entry of allocs
   int64_t bytes = 0;
   // objects
   int64_t* row_ptr = nullptr;
@@ -246,6 +247,7 @@ ivf_status dalloc(ivf_ctx* c, T** p, int64_t count) {
     return fail(c, IVF_E_OOM, buf);
   }
   c->allocs.push_back(q);
+  c->alloc_bytes.push_back((int64_t)bytes);
   c->bytes += (int64_t)bytes;
   *p = static_cast<T*>(q);
   return IVF_OK;
@@ -255,6 +257,9 @@ void dfree(ivf_ctx* c, void* p) {
   if (!p) return;
   auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
   if (it != c->allocs.end()) {
+    const size_t k = (size_t)(it - c->allocs.begin());
+    c->bytes -= c->alloc_bytes[k];
+    c->alloc_bytes.erase(c->alloc_bytes.begin() + (std::ptrdiff_t)k);
     c->allocs.erase(it);
     cudaFree(p);
   }
@@ -774,6 +779,14 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
 
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
+  if (!sh.tc && c->xh) {  // the tensor-core batch buffers are only kept while in use
+    CK(c, cudaStreamSynchronize(c->stream));
+    dfree(c, c->xh);
+    dfree(c, c->rho_h);
+    c->xh = nullptr;
+    c->rho_h = nullptr;
+    c->tc_alloc_rows = c->tc_alloc_batch = c->tc_alloc_kpad = 0;
+  }
   c->shape = sh;
   CK(c, assign_prepare(c->cfg.storage, sh.tile_cap, sh.warps, sh.head_r, sh.head_sub, sh.tc));
   if (sh.head_r > 0) ST(alloc_head(c, sh.head_r));
@@ -945,7 +958,7 @@ ivf_status autotune(ivf_ctx* c) {
     const bool tc_ok = !no_head && c->cfg.storage != IVF_F32 && c->n_inst == 1 && c->kmax > 32 * HEAD_R_LARGE;
     if (tc_ok && (tc_only || !(c->cfg.flags & IVF_FLAG_DENSE_HEAD)))  // DENSE_HEAD: the CUDA-core head
       for (int sub : {1, 2})
-        for (float theta : {0.5f, 0.25f, 0.125f})
+        for (float theta : {0.5f, 0.25f, 0.125f, 0.0625f})
           for (int wp : {4, 8})
             if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_LARGE, theta, sub, true)) cands.push_back(sh);
     if (tc_only && !tc_ok) return fail(c, IVF_E_UNSUPPORTED, "the tensor-core head needs FP16/BF16 storage, one instance and K > 1,024");
