@@ -173,7 +173,19 @@ def _default_stream():
 
 
 class IVF:
-    """One inverted-file spherical k-means problem on the GPU (or a batch of them)."""
+    """One inverted-file spherical k-means problem on the GPU (or a batch of them).
+
+    Arguments mirror ``ivf_config`` (include/ivf.h): ``storage`` is "f32",
+    "f16" or "bf16" (the streamed value type; accumulation is FP32, near-ties
+    are re-scored in FP64 when ``rescore``); ``kernel`` restricts the
+    autotuner to one family -- "auto", "sparse", "dense_head" (CUDA-core dense
+    rows) or "tensor_head" (FP16/BF16: dense rows as a tensor-core GEMM);
+    ``k_tile`` / ``warps_per_block`` fix the launch shape instead of tuning
+    it; ``means_capacity`` and ``dense_head_bytes`` size the first
+    allocations (both grow on demand); ``use_graph`` lets ``iterate`` replay
+    CUDA graphs.  Arrays may be numpy arrays or torch tensors (host or
+    device).
+    """
 
     def __init__(self, row_ptr, term, val, n_terms: int, k: int, storage: str = "f32", rescore: bool = True,
                  empty_policy: int = 0, k_tile: int = 0, warps_per_block: int = 0, validate: bool = False,
