@@ -107,6 +107,9 @@ __device__ __forceinline__ ErrBound err_bound(int m, float nx, int storage, bool
     const float u16 = storage == ST_F16 ? 4.8828125e-04f : 3.90625e-03f;
     const float up = u16 + 2.f * u32;
     c = 2.f * up + up * up;
+    // a tensor-core head part arrives rounded to the storage type: one more
+    // relative u16 on the head products' sum (|H| <= sum of |v u| there)
+    if (tc_head) c += u16;
     sub = storage == ST_F16 ? fm * u32 * (1.f + up) : fm * 1e-37f;
   }
   ErrBound b;
@@ -220,7 +223,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
   const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
   const int32_t* __restrict__ head_slot = a.head_slot;
   // (tensor-core head parts exist for 16-bit storage only)
-  const float* __restrict__ rho_tc = (R > 0 && TC) ? a.rho_head : nullptr;
+  const WT* __restrict__ rho_tc = (R > 0 && TC) ? static_cast<const WT*>(a.rho_head) : nullptr;
   constexpr int RR = R > 0 ? R : 1;
   constexpr int VEC = 16 / (int)sizeof(WT);      // values per 16-byte load of a dense head row
   constexpr int NG = RR >= VEC ? RR / VEC : 1;  // 16-byte groups per lane: clusters VEC*(32g + lane) + k
@@ -456,18 +459,14 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
           }
           if (rho_tc != nullptr) {
             // the head part from the tensor-core GEMM: same lane-to-cluster map
-            const float* __restrict__ rr = rho_tc + (i - a.obj_base) * a.rho_ld + lo + sbase;
+            const WT* __restrict__ rr = rho_tc + (i - a.obj_base) * a.rho_ld + lo + sbase;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
               if (g < ng_live) {
+                float e[VEC];
+                unpack16<WT>(__ldg(reinterpret_cast<const uint4*>(rr + VEC * (32 * g + lane))), e);
 #pragma unroll
-                for (int k4 = 0; k4 < VEC; k4 += 4) {
-                  const float4 h4 = __ldg(reinterpret_cast<const float4*>(rr + VEC * (32 * g + lane) + k4));
-                  acc[g * VEC + k4] = h4.x;
-                  acc[g * VEC + k4 + 1] = h4.y;
-                  acc[g * VEC + k4 + 2] = h4.z;
-                  acc[g * VEC + k4 + 3] = h4.w;
-                }
+                for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = e[k];
               }
             }
           }

@@ -180,12 +180,12 @@ struct ivf_ctx {
   std::vector<ClassPlan> cls;
   bool use_classes = false;
   // tensor-core head: objects in batches of tc_batch; per batch the dense
-  // head values xh [tc_batch x head_max] (16-bit) and the GEMM result
-  // rho_h [tc_batch x kpad] (FP32)
+  // head values xh [tc_batch x head_max] and the GEMM result
+  // rho_h [tc_batch x kpad] (both 16-bit, the storage type)
   cublasHandle_t blas = nullptr;
   void* blas_ws = nullptr;
   void* xh = nullptr;
-  float* rho_h = nullptr;
+  void* rho_h = nullptr;
   int64_t tc_batch = 0;
   int64_t tc_alloc_rows = 0, tc_alloc_kpad = 0, tc_alloc_batch = 0;
   bool tuned = false;
@@ -748,7 +748,7 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
     c->head_max = rows;
   }
   // batches: GEMM output of at most ~3 GB, a multiple of 128 objects
-  c->tc_batch = std::min<int64_t>(c->N, std::max<int64_t>(8192, (int64_t(3) << 30) / (c->kpad * 4)) / 128 * 128);
+  c->tc_batch = std::min<int64_t>(c->N, std::max<int64_t>(8192, (int64_t(3) << 30) / (c->kpad * 2)) / 128 * 128);
   if (c->tc_batch < 1) c->tc_batch = c->N;
   if (!c->xh || c->tc_alloc_rows != rows || c->tc_alloc_batch != c->tc_batch || c->tc_alloc_kpad != c->kpad) {
     dfree(c, c->xh);
@@ -758,7 +758,9 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
     char* x = nullptr;
     ST(dalloc(c, &x, c->tc_batch * rows * 2));
     c->xh = x;
-    ST(dalloc(c, &c->rho_h, c->tc_batch * c->kpad));
+    char* r = nullptr;
+    ST(dalloc(c, &r, c->tc_batch * c->kpad * 2));
+    c->rho_h = r;
     c->tc_alloc_rows = rows;
     c->tc_alloc_batch = c->tc_batch;
     c->tc_alloc_kpad = c->kpad;
@@ -809,16 +811,17 @@ ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
 }
 
 // One batch of the tensor-core head: dense head values of objects
-// [b0, b0 + nb), then rho_h = xh . wd (cuBLAS, FP32 accumulation): rho_h is
-// nb x kpad row-major, i.e. the column-major kpad x nb product of wd^T
-// (kpad x head_max, leading dimension kpad) and xh^T (head_max x nb).
+// [b0, b0 + nb), then rho_h = xh . wd (cuBLAS, FP32 accumulation, output in
+// the storage type): rho_h is nb x kpad row-major, i.e. the column-major
+// kpad x nb product of wd^T (kpad x head_max, leading dimension kpad) and
+// xh^T (head_max x nb).
 ivf_status enqueue_tc_gemm(ivf_ctx* c, int64_t b0, int64_t nb) {
   CK(c, launch_build_xhead(b0, nb, c->row_ptr, c->term, c->val_store, c->head_slot, c->xh, c->head_max, c->stream));
   const cudaDataType dt = c->cfg.storage == IVF_BF16 ? CUDA_R_16BF : CUDA_R_16F;
   const float one = 1.f, zero = 0.f;
   const cublasStatus_t st =
       cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)c->kpad, (int)nb, (int)c->head_max, &one, c->wd, dt,
-                   (int)c->kpad, c->xh, dt, (int)c->head_max, &zero, c->rho_h, CUDA_R_32F, (int)c->kpad,
+                   (int)c->kpad, c->xh, dt, (int)c->head_max, &zero, c->rho_h, dt, (int)c->kpad,
                    CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
   if (st != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasGemmEx failed");
   return IVF_OK;

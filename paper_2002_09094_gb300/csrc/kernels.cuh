@@ -71,9 +71,10 @@ struct AssignArgs {
   int32_t head_sub = 1;         // head sub-tiles of 32 * head_r clusters per shared-memory tile
   // Tensor-core head (16-bit storage): the head part of rho for objects
   // obj_base + o was computed beforehand by a GEMM of the objects' dense head
-  // values with the dense rows, rho_head[o * rho_ld + cluster] (FP32); the
-  // kernel reads it instead of walking the rows.
-  const float* rho_head;
+  // values with the dense rows (FP32 accumulation, stored in the storage
+  // type), rho_head[o * rho_ld + cluster]; the kernel reads it instead of
+  // walking the rows.
+  const void* rho_head;
   int64_t rho_ld;
   int64_t obj_base;
 };
