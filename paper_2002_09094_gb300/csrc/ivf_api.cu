@@ -734,11 +734,11 @@ ivf_status ensure_toff(ivf_ctx* c, int k_tile) {
 }
 
 // Tensor-core head: a fixed number of dense rows (the GEMM depth), sized
-// from the lists that qualify now with a quarter of room, and the per-batch
+// from the lists that qualify now with a tenth of room, and the per-batch
 // buffers; lists beyond the rows are read sparsely (exact).
 ivf_status setup_tc(ivf_ctx* c, long long wanted) {
   const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
-  const int64_t rows = std::min<int64_t>(c->Dt, std::max<int64_t>(64, ((wanted + wanted / 4) + 63) / 64 * 64));
+  const int64_t rows = std::min<int64_t>(c->Dt, std::max<int64_t>(64, ((wanted + wanted / 10) + 63) / 64 * 64));
   if (rows != c->head_max) {
     dfree(c, c->wd);
     c->wd = nullptr;
