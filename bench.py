@@ -358,7 +358,10 @@ def run_ours(args, rank, world, local):
             total_ms = max_over_ranks(total_ms, dist, "cuda")
         # ------------------------------------------------------ end to end
         # each step: host->device copy of the objects from pinned memory, one
-        # iteration, device->host read of the assignment
+        # iteration, device->host read of the assignment.  The copy of step
+        # i + 1 is issued once step i's assignment is enqueued, so it runs on
+        # the context's copy stream while that assignment computes; the first
+        # step's copy is not overlapped.
         rp_h = torch.from_numpy(c.row_ptr).pin_memory()
         tm_h = torch.from_numpy(c.term).pin_memory()
         vl_h = torch.from_numpy(c.val).pin_memory()
@@ -370,9 +373,11 @@ def run_ours(args, rank, world, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.e2e_steps):
-            m.load_objects(rp_h, tm_h, vl_h)
+        m.load_objects(rp_h, tm_h, vl_h)
+        for q in range(args.e2e_steps):
             m.assign(stats=False)
+            if q + 1 < args.e2e_steps:
+                m.load_objects(rp_h, tm_h, vl_h)
             m.update()
             m.get_assign(out_h)
         e1.record(stream)

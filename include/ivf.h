@@ -140,10 +140,19 @@ ivf_status ivf_create(const ivf_config* cfg, const int64_t* row_ptr, const int32
 
 /* Replace the object values and terms (same N and nnz as at create time):
  * the host->device copy of a new batch of objects.  Row structure may
- * change.  Means and assignments are kept.  row_ptr is checked on the device
- * (starts at 0, ends at nnz, non-decreasing) before anything changes, which
- * synchronises once; on IVF_E_INVALID the previous objects stay in place.
- * With IVF_FLAG_VALIDATE the rows are also checked as at create time. */
+ * change.  Means and assignments are kept.
+ * The copy goes to a staging buffer on a second stream of the context, so it
+ * can run while work already on the context stream (an assignment) computes.
+ * The new objects take effect, in stream order, at the next ivf_assign,
+ * ivf_iterate or ivf_set_means_from_docs; ivf_update keeps working on the
+ * objects its assignment ran on.  Device sources are read after the work
+ * already on the context stream; host sources (pinned or pageable) are read
+ * asynchronously and must stay unchanged until one of those three calls (or
+ * ivf_destroy) returns.  A second load before then replaces the first.
+ * row_ptr is checked on the device (starts at 0, ends at nnz, non-decreasing)
+ * before the term and value copies are issued, which synchronises the copy
+ * stream once; on IVF_E_INVALID the current objects stay in place.  With
+ * IVF_FLAG_VALIDATE the rows are also checked as at create time. */
 ivf_status ivf_load_objects(ivf_ctx* ctx, const int64_t* row_ptr, const int32_t* term,
                             const float* val);
 

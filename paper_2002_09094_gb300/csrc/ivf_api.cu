@@ -104,6 +104,17 @@ struct ivf_ctx {
   float* val32 = nullptr;
   void* val_store = nullptr;
   float* nx = nullptr;
+  // staging copy of the objects for ivf_load_objects: filled on copy_stream
+  // (ev_staged), moved into place on the context stream by commit_objects
+  // (ev_staging_free once those device copies ran)
+  bool staging_ready = false;
+  bool objects_pending = false;
+  int64_t* st_row_ptr = nullptr;
+  int32_t* st_term = nullptr;
+  float* st_val32 = nullptr;
+  unsigned* d_load_status = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_src = nullptr, ev_staged = nullptr, ev_staging_free = nullptr;
   int64_t* inst_docs = nullptr;
   int32_t* inst_clu = nullptr;
   int64_t* inst_toff = nullptr;
@@ -623,6 +634,53 @@ ivf_status grow_head_if_needed(ivf_ctx* c, long long wanted) {
   c->head_max = rows;
   drop_graphs(c);
   CK(c, launch_build_head(ivf_args(c, c->mcur), c->stream));
+  return IVF_OK;
+}
+
+// Staging buffers, copy stream and events of ivf_load_objects (on first use).
+ivf_status ensure_staging(ivf_ctx* c) {
+  if (c->staging_ready) return IVF_OK;
+  ST(dalloc(c, &c->st_row_ptr, c->N + 1));
+  ST(dalloc(c, &c->st_term, c->nnz));
+  ST(dalloc(c, &c->st_val32, c->nnz));
+  ST(dalloc(c, &c->d_load_status, 1));
+  if (!c->copy_stream) CK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&c->ev_src, &c->ev_staged, &c->ev_staging_free})
+    if (!*e) CK(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  c->staging_ready = true;
+  return IVF_OK;
+}
+
+bool device_resident(const void* p) {
+  cudaPointerAttributes at{};
+  if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Objects loaded by ivf_load_objects take effect here, in stream order: the
+// context stream waits for the staging copy, copies it into place (device to
+// device) and prepares it as at create time.  Called by the calls that start
+// from the objects (assignment, iterate, initial means from documents); the
+// update step keeps working on the objects its assignment ran on.
+ivf_status commit_objects(ivf_ctx* c) {
+  if (!c->objects_pending) return IVF_OK;
+  c->objects_pending = false;
+  cudaStream_t s = c->stream;
+  CK(c, cudaStreamWaitEvent(s, c->ev_staged, 0));
+  CK(c, cudaMemcpyAsync(c->row_ptr, c->st_row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemcpyAsync(c->term, c->st_term, sizeof(int32_t) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaMemcpyAsync(c->val32, c->st_val32, sizeof(float) * c->nnz, cudaMemcpyDeviceToDevice, s));
+  CK(c, cudaEventRecord(c->ev_staging_free, s));
+  CK(c, cudaMemsetAsync(&c->dc->negative, 0, sizeof(unsigned), s));
+  CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->val32,
+                               c->cfg.storage == IVF_F32 ? nullptr : c->val_store, c->cfg.storage, c->nx, c->n_inst,
+                               c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
+                               &c->dc->status, &c->dc->negative, s));
+  if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
+  c->members_valid = false;
   return IVF_OK;
 }
 
@@ -1329,6 +1387,12 @@ const char* ivf_last_error(const ivf_ctx* ctx) { return ctx ? ctx->err.c_str() :
 void ivf_destroy(ivf_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
+  if (ctx->copy_stream) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    cudaStreamDestroy(ctx->copy_stream);
+  }
+  for (cudaEvent_t ev : {ctx->ev_src, ctx->ev_staged, ctx->ev_staging_free})
+    if (ev) cudaEventDestroy(ev);
   drop_graphs(ctx);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
   for (auto& ev : ctx->ev)
@@ -1382,31 +1446,29 @@ ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* ins
 
 ivf_status ivf_load_objects(ivf_ctx* c, const int64_t* row_ptr, const int32_t* term, const float* val) {
   if (!c || !row_ptr || (c->nnz > 0 && (!term || !val))) return fail(c, IVF_E_INVALID, "null argument");
-  cudaStream_t s = c->stream;
-  // row_ptr is checked on the device, in scratch, before the context's copy
-  // changes: the one synchronisation of this call.
-  int64_t* rp_new = reinterpret_cast<int64_t*>(c->k64a);  // scratch_len >= N + 1
-  CK(c, cudaMemcpyAsync(rp_new, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, s));
-  CK(c, launch_check_row_ptr(rp_new, c->N, c->nnz, &c->dc->status, s));
-  {
-    unsigned st = 0;
-    CK(c, cudaMemcpyAsync(&st, &c->dc->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
-    CK(c, cudaStreamSynchronize(s));
-    if (st & STS_BAD_ROWS) {
-      CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), s));
-      return fail(c, IVF_E_INVALID, "row_ptr must start at 0, end at nnz and be non-decreasing");
-    }
+  ST(ensure_staging(c));
+  cudaStream_t cs = c->copy_stream;
+  c->objects_pending = false;  // a load not yet committed is replaced
+  // the staging copy is free once the last commit's device copies ran
+  CK(c, cudaStreamWaitEvent(cs, c->ev_staging_free, 0));
+  // device sources are read after the work already on the context stream
+  if (device_resident(row_ptr) || device_resident(term) || device_resident(val)) {
+    CK(c, cudaEventRecord(c->ev_src, c->stream));
+    CK(c, cudaStreamWaitEvent(cs, c->ev_src, 0));
   }
-  CK(c, cudaMemcpyAsync(c->row_ptr, rp_new, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToDevice, s));
-  CK(c, cudaMemcpyAsync(c->term, term, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, s));
-  CK(c, cudaMemcpyAsync(c->val32, val, sizeof(float) * c->nnz, cudaMemcpyDefault, s));
-  CK(c, cudaMemsetAsync(&c->dc->negative, 0, sizeof(unsigned), s));
-  CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->val32,
-                               c->cfg.storage == IVF_F32 ? nullptr : c->val_store, c->cfg.storage, c->nx, c->n_inst,
-                               c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
-                               &c->dc->status, &c->dc->negative, s));
-  if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
-  c->members_valid = false;
+  // row_ptr is checked on the device before the big copies are issued: the
+  // one synchronisation of this call (on the copy stream only)
+  CK(c, cudaMemcpyAsync(c->st_row_ptr, row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDefault, cs));
+  CK(c, cudaMemsetAsync(c->d_load_status, 0, sizeof(unsigned), cs));
+  CK(c, launch_check_row_ptr(c->st_row_ptr, c->N, c->nnz, c->d_load_status, cs));
+  unsigned st = 0;
+  CK(c, cudaMemcpyAsync(&st, c->d_load_status, sizeof(unsigned), cudaMemcpyDeviceToHost, cs));
+  CK(c, cudaStreamSynchronize(cs));
+  if (st & STS_BAD_ROWS) return fail(c, IVF_E_INVALID, "row_ptr must start at 0, end at nnz and be non-decreasing");
+  CK(c, cudaMemcpyAsync(c->st_term, term, sizeof(int32_t) * c->nnz, cudaMemcpyDefault, cs));
+  CK(c, cudaMemcpyAsync(c->st_val32, val, sizeof(float) * c->nnz, cudaMemcpyDefault, cs));
+  CK(c, cudaEventRecord(c->ev_staged, cs));
+  c->objects_pending = true;
   return IVF_OK;
 }
 
@@ -1464,6 +1526,7 @@ ivf_status ivf_restore_means(ivf_ctx* c, const int64_t* ptr, const int32_t* term
 
 ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
   if (!c || !doc_ids) return fail(c, IVF_E_INVALID, "null argument");
+  ST(commit_objects(c));
   std::vector<int32_t> ids(c->Kt);
   CK(c, cudaMemcpy(ids.data(), doc_ids, sizeof(int32_t) * c->Kt, cudaMemcpyDefault));
   // local -> global object ids; distinct within each instance
@@ -1479,7 +1542,8 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
   }
   // row lengths on the host to size the means
   std::vector<int64_t> hrp(c->N + 1);
-  CK(c, cudaMemcpy(hrp.data(), c->row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToHost));
+  CK(c, cudaMemcpyAsync(hrp.data(), c->row_ptr, sizeof(int64_t) * (c->N + 1), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
   int64_t e0 = 0;
   for (int64_t j = 0; j < c->Kt; ++j) e0 += hrp[ids[j] + 1] - hrp[ids[j]];
   ST(ensure_capacity(c, e0));
@@ -1499,6 +1563,7 @@ ivf_status ivf_set_means_from_docs(ivf_ctx* c, const int32_t* doc_ids) {
 ivf_status ivf_assign(ivf_ctx* c, int32_t* assign_out, float* best_out, float* gap_out, ivf_iter_stats* stats_out) {
   if (!c) return IVF_E_INVALID;
   if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  ST(commit_objects(c));
   if (needs_tuning(c)) ST(autotune(c));
   const int target = c->alatest < 0 ? 0 : (c->alatest ^ 1);
   const int prev = c->alatest;
@@ -1543,6 +1608,7 @@ ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_
   if (!c) return IVF_E_INVALID;
   if (max_iter < 0) return fail(c, IVF_E_INVALID, "max_iter < 0");
   if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  ST(commit_objects(c));
   if (needs_tuning(c)) ST(autotune(c));
   int32_t done = 0, conv = 0;
   const bool use_graph = !(c->cfg.flags & IVF_FLAG_NO_GRAPH);

@@ -193,6 +193,7 @@ class IVF:
                  dense_head_bytes: int = 0, _batched=None):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p(0)
+        self._loading = None
         rp, rk = _ptr(row_ptr, np.int64)
         tp, tk = _ptr(term, np.int32)
         vptr, vk = _ptr(val, np.float32)
@@ -234,6 +235,7 @@ class IVF:
         if self._ctx:
             self._lib.ivf_destroy(self._ctx)
             self._ctx = ctypes.c_void_p(0)
+        self._loading = None
 
     def __del__(self):
         try:
@@ -249,10 +251,15 @@ class IVF:
 
     # -- calls
     def load_objects(self, row_ptr, term, val):
+        """New objects (same N and nnz), copied on a second stream; they take
+        effect at the next assign / iterate / set_means_from_docs, and update()
+        keeps working on the objects of the last assignment.  The sources are
+        held until then (a pinned host buffer is read asynchronously)."""
         rp, rk = _ptr(row_ptr, np.int64)
         tp, tk = _ptr(term, np.int32)
         vp, vk = _ptr(val, np.float32)
         self._check(self._lib.ivf_load_objects(self._ctx, rp, tp, vp))
+        self._loading = (rk, tk, vk)
 
     def set_means(self, mean_ptr, mean_term, mean_val):
         pp, pk = _ptr(mean_ptr, np.int64)
@@ -263,6 +270,7 @@ class IVF:
     def set_means_from_docs(self, doc_ids):
         dp, dk = _ptr(doc_ids, np.int32)
         self._check(self._lib.ivf_set_means_from_docs(self._ctx, dp))
+        self._loading = None
 
     def assign(self, assign_out=None, best_out=None, gap_out=None, stats: bool = True):
         """Assignment step; outputs are optional CUDA tensors. Returns stats dict (or None)."""
@@ -271,6 +279,7 @@ class IVF:
         bp = best_out.data_ptr() if best_out is not None else 0
         gp = gap_out.data_ptr() if gap_out is not None else 0
         self._check(self._lib.ivf_assign(self._ctx, ap, bp, gp, ctypes.byref(st) if stats else None))
+        self._loading = None
         return st.as_dict() if stats else None
 
     def update(self):
@@ -281,6 +290,7 @@ class IVF:
         st = IterStats()
         self._check(self._lib.ivf_iterate(self._ctx, int(max_iter), ctypes.byref(done), ctypes.byref(conv),
                                           ctypes.byref(st)))
+        self._loading = None
         return int(done.value), bool(conv.value), st.as_dict()
 
     def get_assign(self, out=None) -> np.ndarray:

@@ -650,6 +650,55 @@ def test_load_objects_rejects_bad_row_ptr_and_stays_usable():
         assert np.array_equal(m.get_assign(), a0)
 
 
+@pytest.mark.parametrize("source", ["numpy", "pinned", "device"])
+def test_load_objects_overlapped_with_the_iteration(source):
+    """A load issued right after an assignment is enqueued (its copy runs on
+    the context's copy stream meanwhile) takes effect at the next assignment;
+    the update in between works on the objects its assignment ran on, and of
+    two loads the second wins.  Bit-equal to the same calls made one after
+    the other with nothing pending."""
+    import torch
+
+    a = corpus_for(3000, 3000, mean_len=25.0, seed=35)
+    # the same rows in another order: same N and nnz, other objects per id
+    perm = np.random.default_rng(35).permutation(a.n_docs)
+    lens = np.diff(a.row_ptr)
+    b_ptr = np.concatenate([[0], np.cumsum(lens[perm])]).astype(np.int64)
+    b_term = np.concatenate([a.term[a.row_ptr[i]:a.row_ptr[i + 1]] for i in perm]).astype(np.int32)
+    b_val = np.concatenate([a.val[a.row_ptr[i]:a.row_ptr[i + 1]] for i in perm]).astype(np.float32)
+    half = (a.val * 0.5).astype(np.float32)
+    k = 80
+    ids = dg.init_doc_ids(a.n_docs, k, 35)
+
+    def src(x):
+        if source == "numpy":
+            return x
+        t = torch.from_numpy(np.ascontiguousarray(x))
+        return t.pin_memory() if source == "pinned" else t.cuda()
+
+    def run(mode):
+        with ivf.IVF(a.row_ptr, a.term, a.val, a.n_terms, k) as m:
+            m.set_means_from_docs(ids)
+            m.assign()
+            if mode == "overlapped":
+                m.load_objects(src(a.row_ptr), src(a.term), src(half))  # replaced by the next load
+                m.load_objects(src(b_ptr), src(b_term), src(b_val))
+            m.update()
+            if mode == "sequential":
+                m.load_objects(b_ptr, b_term, b_val)
+            m.assign()
+            out = [m.get_assign(), m.get_best()]
+            m.update()
+            m.assign()
+            out.append(m.get_assign())
+            return out
+
+    got, ref, none = run("overlapped"), run("sequential"), run("no load")
+    for x, y in zip(got, ref):
+        assert np.array_equal(x.view(np.uint32), y.view(np.uint32))
+    assert not np.array_equal(got[0], none[0])
+
+
 @pytest.mark.parametrize("k,kind", [(1500, "poisson"), (4500, "poisson"), (3000, "lognormal")])
 def test_dense_head_wide_tiles_bit_equal(k, kind):
     """Shared-memory tiles of 1, 2 and 4 head sub-tiles (the sparse lists
