@@ -490,14 +490,18 @@ def run_batched(args, rank, world, local):
                            storage=args.storage, stream=stream.cuda_stream)
         del term, val
         m.set_means_from_docs(np.concatenate(ids))
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
         m.iterate(args.warmup)
         launches0 = ivf.launch_count()
         torch.cuda.synchronize()
+        t_begin = time.time()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         done, conv, st = m.iterate(iters)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk = clocks.stop(t_begin, time.time())
         batched_ms = e0.elapsed_time(e1) / max(1, done)
         launches = ivf.launch_count() - launches0
         a_batched = m.get_assign()
@@ -535,6 +539,16 @@ def run_batched(args, rank, world, local):
                 s1.timing_reset(False)
                 for key in seq_ph:
                     seq_ph[key] += t1[key + "_ms"]
+    # roofline of the assignment launches of the eager iteration (all classes)
+    bv = 4 if args.storage == "f32" else 2
+    n_all, nnz_all = int(inst_docs[-1]), int(offs[-1])
+    b_assign = nnz_all * (4 + bv) + 8 * (n_all + 1) + int(tph["entries_visited"]) * (2 + bv) + n_all * 12
+    peak, peak_kind = peaks()
+    achieved = b_assign / (tph["assign_kernel_ms"] / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_assign (one launch per class)",
+            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": int(b_assign),
+            "entries_per_launch": int(tph["entries_visited"]), "kernel_ms": round(tph["assign_kernel_ms"], 4)}
     out = {"metric": METRIC, "value": batched_ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": int(done),
            "warmup": args.warmup, "ms_per_step": round(batched_ms, 4), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
@@ -551,7 +565,9 @@ def run_batched(args, rank, world, local):
            if info["dense_head_r"] else "sparse",
            "sequential_s_per_iter": seq_ms / 1e3, "batched_speedup": round(seq_ms / batched_ms, 3),
            "sequential_phases_ms_one_eager_iteration": {k_: round(v_, 3) for k_, v_ in seq_ph.items()},
-           "equal_assignments": equal, "converged": bool(conv), "gpu_launches": int(launches)}
+           "equal_assignments": equal, "converged": bool(conv), "roofline": roof,
+           # the host-to-device leg is measured on the single-instance line
+           "e2e": None, "gpu_launches": int(launches), "clocks": clk}
     if rank == 0:
         emit(out)
 

@@ -209,7 +209,7 @@ struct ivf_ctx {
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   long long graph_kernels[2][2] = {{0, 0}, {0, 0}};
   bool own_stream = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // assignment start / end
   // timing window: event pool and per-call records
   bool timing = false;
   std::vector<cudaEvent_t> tev;
