@@ -51,7 +51,7 @@ typedef enum {
   IVF_E_OOM = 3,         /* device allocation failed or a capacity was exceeded */
   IVF_E_CUDA = 4,        /* a CUDA call failed; destroy the context */
   IVF_E_TIMEOUT = 5,     /* a bounded device wait ran out */
-  IVF_E_UNSUPPORTED = 6  /* valid request this build does not handle */
+  IVF_E_UNSUPPORTED = 6  /* valid request the library does not handle */
 } ivf_status;
 
 /* Storage type of the object and mean values streamed by the assignment

@@ -18,7 +18,7 @@ What it computes, and where the paper says so:
     assignment used.  Lloyd never decreases it.
   * Multiplication count of IVF (Eq. 15): sum_i sum_h (nc)_{t_(i,h)}.
 
-Readings where the paper is silent or inconsistent (each also in the design doc):
+Readings where the paper is silent or inconsistent (the CUDA path takes the same):
   R1 ties: the smallest cluster id among all maxima.  Algorithm 3 scans j
      upward with a strict '>' (first maximum wins); Algorithm 2 starts from
      the current assignment.  The stateless lowest-id rule is used.

@@ -1,8 +1,9 @@
 """Build libivfkm.so (CUDA, sm_103a) in-tree with nvcc.
 
 Each translation unit under csrc/ is compiled in parallel, then linked into
-``paper_2002_09094_gb300/libivfkm.so`` (static cudart, so the library needs
-only the driver at run time).  Nothing is installed into site-packages.
+``paper_2002_09094_gb300/libivfkm.so`` (CUDA runtime linked statically; at
+run time the library needs the CUDA driver and cuBLAS).  Nothing is installed
+into site-packages.
 """
 from __future__ import annotations
 
