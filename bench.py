@@ -51,10 +51,15 @@ def parse():
     p.add_argument("--kernel", choices=["auto", "dense_head", "sparse", "tensor_head"], default="auto",
                    help="assignment kernel family (auto = the autotuner picks)")
     p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=0,
+                   help="steps of the end-to-end leg (0 = as many as --steps)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
+
+
+def e2e_steps(args) -> int:
+    return args.e2e_steps if args.e2e_steps > 0 else max(1, args.steps)
 
 
 def dist_env():
@@ -380,15 +385,16 @@ def run_ours(args, rank, world, local):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         m.load_objects(rp_h, tm_h, vl_h)
-        for q in range(args.e2e_steps):
+        n_e2e = e2e_steps(args)
+        for q in range(n_e2e):
             m.assign(stats=False)
-            if q + 1 < args.e2e_steps:
+            if q + 1 < n_e2e:
                 m.load_objects(rp_h, tm_h, vl_h)
             m.update()
             m.get_assign(out_h)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / max(1, args.e2e_steps)
+        e2e_ms = e0.elapsed_time(e1) / n_e2e
         # current state for the CPU baseline sample
         means_np = m.get_means()
         assign_np = m.get_assign()
@@ -397,7 +403,7 @@ def run_ours(args, rank, world, local):
         # same number of iterations from the same initial means in FP32
         equal_f32 = None
         if args.storage != "f32":
-            cycles = args.warmup + args.steps + args.e2e_steps + 1
+            cycles = args.warmup + args.steps + n_e2e + 1
             with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage="f32",
                          stream=stream.cuda_stream) as m32:
                 m32.set_means_from_docs(ids)
@@ -441,7 +447,7 @@ def run_ours(args, rank, world, local):
                                   "update": round(timing["update_ms"] / max(1, timing["n_update"]), 4)},
            "roofline": roof,
            "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)},
+                   "d2h_bytes_per_step": int(d2h), "steps": n_e2e},
            "gpu_launches": int(launches), "clocks": clk}
     if equal_f32 is not None:
         out["assignments_vs_f32"] = equal_f32
