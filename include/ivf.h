@@ -19,11 +19,15 @@
  * Conventions (all calls):
  *   - Ids are 0-based (the paper counts from 1).
  *   - Input arrays may be host or device pointers (the library copies them
- *     with cudaMemcpyDefault); the library never keeps a caller pointer.
+ *     with cudaMemcpyDefault); the library keeps no caller pointer after a
+ *     call returns, except that ivf_load_objects reads its sources until the
+ *     next ivf_assign / ivf_iterate / ivf_set_means_from_docs returns.
  *     Output arrays of ivf_assign are DEVICE pointers (or NULL); the
  *     ivf_get_* calls write to host or device pointers.
  *   - Every call is ordered on the CUDA stream given at create time and
- *     returns after enqueueing, except where a comment says it synchronises.
+ *     returns after enqueueing, except where a comment says it synchronises
+ *     (ivf_load_objects copies on a second stream of the context, ordered
+ *     with the first as its comment says).
  *   - Errors come back as an ivf_status; the library never aborts or traps.
  *     After IVF_E_INVALID or IVF_E_STATE the context is unchanged and still
  *     usable; after IVF_E_CUDA destroy it.  ivf_last_error() gives a message.
