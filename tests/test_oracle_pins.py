@@ -166,6 +166,17 @@ def check_duplicate_means_tie():
     assert not np.any(a == 2)  # the lower id of the tied pair always wins
     tied = a == 0
     assert np.all(gap[tied] == 0.0)
+    # cluster 2 is therefore empty: policy 0 keeps its previous mean exactly,
+    # policy 1 leaves it with no terms; the other rows are the same in both
+    m0, norm0, sizes0 = sk.update(c, a, m, empty_policy=0)
+    m1, norm1, sizes1 = sk.update(c, a, m, empty_policy=1)
+    assert sizes0[2] == 0 and norm0[2] == 0.0
+    pt, pv = m0.row(2)
+    qt, qv = m.row(2)
+    assert np.array_equal(pt, qt) and np.array_equal(pv, qv)
+    assert m1.row(2)[0].size == 0
+    for j in (0, 1, 3):
+        assert np.array_equal(m0.row(j)[0], m1.row(j)[0]) and np.array_equal(m0.row(j)[1], m1.row(j)[1])
 
 
 def check_zero_similarity_object():
@@ -302,8 +313,41 @@ def _mut_gap_sign(orig):
     return "assign_from_similarities", assign_from_similarities
 
 
+def _mut_empty_loses_mean(orig):
+    def update(corpus, assign, prev, empty_policy=0):
+        return orig(corpus, assign, prev, 1)   # empty clusters never keep their previous mean
+    return "update", update
+
+
+def _mut_shifted_object(orig):
+    def cluster_sums(corpus, assign, k):
+        a = np.asarray(assign)
+        return orig(corpus, np.roll(a, 1), k)  # x_{i} summed into the cluster of x_{i-1}
+    return "cluster_sums", cluster_sums
+
+
+def _mut_negated_similarity(orig):
+    def similarities(corpus, means, rows=None, chunk=2048):
+        return -orig(corpus, means, rows, chunk)
+    return "similarities", similarities
+
+
+def _mut_count_per_term_not_per_entry(orig):
+    def multiplication_count(corpus, means):
+        return int(corpus.nnz)                 # one product per object term instead of per posting entry
+    return "multiplication_count", multiplication_count
+
+
+def _mut_no_update(orig):
+    def update(corpus, assign, prev, empty_policy=0):
+        m, norm, sizes = orig(corpus, assign, prev, empty_policy)
+        return prev, norm, sizes               # means never move
+    return "update", update
+
+
 MUTANTS = [_mut_drop_last_term, _mut_highest_id_ties, _mut_no_normalisation, _mut_shifted_cluster,
-           _mut_reversed_means, _mut_gap_sign]
+           _mut_reversed_means, _mut_gap_sign, _mut_empty_loses_mean, _mut_shifted_object,
+           _mut_negated_similarity, _mut_count_per_term_not_per_entry, _mut_no_update]
 
 
 @pytest.mark.parametrize("mutant", MUTANTS, ids=[m.__name__ for m in MUTANTS])
@@ -324,4 +368,7 @@ def name_of(mutant):
         _mut_drop_last_term: "similarities", _mut_highest_id_ties: "assign_from_similarities",
         _mut_no_normalisation: "update", _mut_shifted_cluster: "cluster_sums",
         _mut_reversed_means: "similarities", _mut_gap_sign: "assign_from_similarities",
+        _mut_empty_loses_mean: "update", _mut_shifted_object: "cluster_sums",
+        _mut_negated_similarity: "similarities", _mut_count_per_term_not_per_entry: "multiplication_count",
+        _mut_no_update: "update",
     }[mutant]
