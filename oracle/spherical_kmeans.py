@@ -23,7 +23,8 @@ Readings where the paper is silent or inconsistent (the CUDA path takes the same
      upward with a strict '>' (first maximum wins); Algorithm 2 starts from
      the current assignment.  The stateless lowest-id rule is used.
   R2 an object sharing no term with any mean has rho = 0 everywhere and so
-     goes to cluster 0 under R1 (Algorithm 3 would leave it unassigned).
+     goes to cluster 0 under R1 (Algorithm 3 would leave it unassigned);
+     n_zero_sim counts these objects (zero_similarity_objects).
   R3 a cluster with no members, or whose member sum is exactly zero, keeps
      its previous mean (empty_policy 0) or becomes an empty mean with no
      terms (empty_policy 1); the paper's w/|C_j| would be 0/0.
@@ -204,6 +205,20 @@ def update(corpus, assign, prev: Means, empty_policy: int = 0):
     return Means(ptr=ptr, term=term, val=val, n_terms=prev.n_terms), norm, sizes
 
 
+def zero_similarity_objects(corpus, means: Means) -> np.ndarray:
+    """Mask of the objects that share no term with any mean (reading R2).
+
+    These are the objects for which Algorithm 3's inner loop over posting
+    entries never runs, so it never assigns them: sum_h (nc)_{t_(i,h)} = 0.
+    An object that shares terms but whose similarities all come out 0 (signed
+    values that cancel) is not one of them.
+    """
+    nc = np.bincount(means.term, minlength=corpus.n_terms).astype(np.int64)
+    owner = np.repeat(np.arange(corpus.n_docs), np.diff(corpus.row_ptr))
+    per_obj = np.bincount(owner, weights=nc[corpus.term], minlength=corpus.n_docs)
+    return per_obj == 0
+
+
 def objective(best) -> float:
     """J = sum_i x_i . mu_{a_i} (Eq. 5) accumulated in FP64."""
     return float(np.sum(np.asarray(best, dtype=np.float64)))
@@ -249,7 +264,7 @@ def iterate(corpus, means0: Means, max_iter: int, empty_policy: int = 0,
         rho = similarities(corpus, means)
         a, best, gap = assign_from_similarities(rho)
         n_changed = corpus.n_docs if prev is None else int(np.count_nonzero(a != prev))
-        n_zero = int(np.count_nonzero(np.all(rho == 0.0, axis=1)))
+        n_zero = int(np.count_nonzero(zero_similarity_objects(corpus, means)))
         mc = multiplication_count(corpus, means)
         new_means, norm, sizes = update(corpus, a, means, empty_policy)
         out.append(Iteration(r=r, assign=a, best=best, gap=gap, objective=objective(best),

@@ -182,9 +182,22 @@ def check_duplicate_means_tie():
 def check_zero_similarity_object():
     rows = [([0], [1.0]), ([1], [1.0]), ([3], [1.0])]
     c = dg.corpus_from_rows(rows, 4)
-    rho = sk.similarities(c, sk.initial_means(c, [1, 0]))
+    m = sk.initial_means(c, [1, 0])
+    rho = sk.similarities(c, m)
     a, best, gap = sk.assign_from_similarities(rho)
     assert a.tolist() == [1, 0, 0] and best[2] == 0.0 and gap[2] == 0.0
+    assert sk.zero_similarity_objects(c, m).tolist() == [False, False, True]
+    # signed values: object 0 shares both terms with mean 0 = (1, -1)/sqrt(2)
+    # and one with mean 1 = (-1, 0), yet 0.5 a - 0.5 a = 0 exactly and
+    # 0.5 * (-1) < 0, so its best is 0; it met posting entries and is not
+    # counted.  Object 1 (term 5) shares nothing, object 2 (no terms) neither.
+    c2 = dg.corpus_from_rows([([0, 1], [0.5, 0.5]), ([5], [1.0]), ([], [])], 6)
+    m2 = sk.means_from_rows([0, 2, 3], [0, 1, 0], [1.0, -1.0, -1.0], 6)
+    rho2 = sk.similarities(c2, m2)
+    assert rho2[0, 0] == 0.0 and rho2[0, 1] < 0.0
+    its = sk.iterate(c2, m2, max_iter=1)
+    assert sk.zero_similarity_objects(c2, m2).tolist() == [False, True, True]
+    assert its[0].n_zero_sim == 2 and its[0].best[0] == 0.0
 
 
 def check_lloyd_invariants(seed=8):
@@ -250,10 +263,93 @@ def check_multiplication_count(seed=13):
     assert int(nc.sum()) == int(m.ptr[-1])
 
 
+def _brute_force_assignment(rows_dense, mus):
+    """Plain-Python similarities, lowest-id argmax, best and top-2 gap."""
+    out = []
+    for x in rows_dense:
+        rho = [sum(a * b for a, b in zip(x, mu)) for mu in mus]
+        order = sorted(range(len(mus)), key=lambda j: (-rho[j], j))
+        out.append((order[0], rho[order[0]], rho[order[0]] - rho[order[1]]))
+    return out
+
+
+def check_lockstep_checker(seed=17):
+    """The lockstep comparison of a GPU assignment with the FP64 argmax under
+    the same means (the per-iteration protocol on Algorithm 2's assignment,
+    Eq. 4) counts exactly the planted disagreements.
+
+    Expected values come from a plain-Python brute force: means
+    mu_j = x_{d_j} / ||x_{d_j}|| with a duplicated mean (exact ties, gap 0),
+    plus a hand-built pair of means 5e-9 apart in similarity (a near-tie
+    below the 1e-6 exclusion) and an object sharing no term with any mean.
+    """
+    c = tiny_corpus(seed, n_docs=70)
+    ids = [int(d) for d in dg.init_doc_ids(c.n_docs, 5, seed)]
+    ids = ids + [ids[1]]                                   # mean 5 duplicates mean 1
+    X = dense_rows(c)
+    mus = []
+    for d in ids:
+        nrm = math.sqrt(sum(v * v for v in X[d]))
+        mus.append([v / nrm for v in X[d]])
+    bf = _brute_force_assignment(X, mus)
+    a_bf = np.array([t[0] for t in bf], dtype=np.int32)
+    best_bf = np.array([t[1] for t in bf])
+    gap_bf = np.array([t[2] for t in bf])
+    excl_bf = gap_bf < 1e-6
+    assert excl_bf.any() and (~excl_bf).sum() > 20
+    means = sk.initial_means(c, ids)
+
+    # 1. the true assignment: nothing flagged; exactly the near-ties excluded
+    rep = sk.lockstep_check(c, means, a_bf, best_bf)
+    assert rep["checked"] == c.n_docs and rep["mismatches"] == 0
+    assert rep["excluded"] == int(excl_bf.sum())
+    assert rep["best_ok"] and rep["max_best_err"] <= 1e-12
+
+    # 2. wrong clusters on clear objects are counted, on excluded ones ignored
+    clear = np.flatnonzero(~excl_bf)
+    wrong = clear[::4]
+    ga = a_bf.copy()
+    ga[wrong] = (ga[wrong] + 1) % len(ids)
+    ga[np.flatnonzero(excl_bf)] = (a_bf[excl_bf] + 2) % len(ids)
+    rep = sk.lockstep_check(c, means, ga, best_bf)
+    assert rep["mismatches"] == wrong.size
+    assert rep["mismatch_rows"] == sorted(wrong.tolist())[:20]
+
+    # 3. a row subset reads the full-length outputs at those rows: every other
+    #    position holds an invalid cluster id and a wrong best
+    rows = np.arange(c.n_docs - 1, -1, -3)
+    ga = np.full(c.n_docs, -1, dtype=np.int32)
+    gb = np.full(c.n_docs, 5.0)
+    ga[rows] = a_bf[rows]
+    gb[rows] = best_bf[rows]
+    rep = sk.lockstep_check(c, means, ga, gb, rows=rows)
+    assert rep["checked"] == rows.size and rep["mismatches"] == 0 and rep["best_ok"]
+    assert rep["excluded"] == int(excl_bf[rows].sum())
+    ga[rows[1]] = (a_bf[rows[1]] + 1) % len(ids)
+    if not excl_bf[rows[1]]:
+        assert sk.lockstep_check(c, means, ga, gb, rows=rows)["mismatches"] == 1
+
+    # 4. the best-similarity tolerance: 2e-5 off fails, 5e-6 off passes
+    j = int(clear[0])
+    gb = best_bf.copy()
+    gb[j] += 2e-5
+    rep = sk.lockstep_check(c, means, a_bf, gb)
+    assert not rep["best_ok"] and abs(rep["max_best_err"] - 2e-5) < 1e-12
+    gb[j] = best_bf[j] - 5e-6
+    assert sk.lockstep_check(c, means, a_bf, gb)["best_ok"]
+
+    # 5. a hand-built near-tie (gap 1 - 1/sqrt(1 + 1e-8) ~ 5e-9) and an
+    #    object with no shared term (gap 0) are excluded; a gap of ~8e-5 is not
+    c2 = dg.corpus_from_rows([([0], [1.0]), ([0, 1], [0.6, 0.8]), ([2], [1.0])], 3)
+    m2 = sk.means_from_rows([0, 1, 3], [0, 0, 1], [1.0, 1.0, 1e-4], 3)
+    rep = sk.lockstep_check(c2, m2, [1, 0, 1], [1.0, 0.6, 0.0])
+    assert rep["excluded"] == 2 and rep["mismatches"] == 1 and rep["mismatch_rows"] == [1]
+
+
 CHECKS = [check_golden, check_euclidean_brute_force, check_dense_equals_sparse, check_k1,
           check_n_equals_k, check_disjoint_supports, check_duplicate_means_tie,
           check_zero_similarity_object, check_lloyd_invariants, check_ivf_equals_lloyd,
-          check_multiplication_count]
+          check_multiplication_count, check_lockstep_checker]
 
 
 @pytest.mark.parametrize("check", CHECKS, ids=[f.__name__ for f in CHECKS])
@@ -345,9 +441,54 @@ def _mut_no_update(orig):
     return "update", update
 
 
+def _lockstep_with(bug):
+    """lockstep_check restated with one planted slip."""
+    def lockstep_check(corpus, means_prev, gpu_assign, gpu_best=None, rows=None,
+                       gap_exclusion=1e-6, best_tol=1e-5):
+        rows_arr = np.arange(corpus.n_docs) if rows is None else np.asarray(rows, dtype=np.int64)
+        a, best, gap = sk.assign_from_similarities(sk.similarities(corpus, means_prev, rows_arr))
+        if bug == "unindexed":
+            ga = np.asarray(gpu_assign)[:rows_arr.size]
+        else:
+            ga = np.asarray(gpu_assign)[rows_arr]
+        excluded = gap >= gap_exclusion if bug == "inverted_exclusion" else gap < gap_exclusion
+        mism = (ga != a) & ~excluded
+        rep = {"checked": int(rows_arr.size), "excluded": int(excluded.sum()),
+               "mismatches": int(mism.sum()), "mismatch_rows": rows_arr[mism][:20].tolist()}
+        if gpu_best is not None:
+            gb = np.asarray(gpu_best, dtype=np.float64)
+            gb = gb[:rows_arr.size] if bug == "unindexed" else gb[rows_arr]
+            rep["max_best_err"] = float(np.max(np.abs(gb - best))) if rows_arr.size else 0.0
+            rep["best_ok"] = True if bug == "best_tol_ignored" else rep["max_best_err"] <= best_tol
+        rep["oracle_assign"], rep["oracle_best"], rep["oracle_gap"] = a, best, gap
+        return rep
+    return lockstep_check
+
+
+def _mut_zero_sim_by_best_value(orig):
+    def zero_similarity_objects(corpus, means):
+        _, best, _ = sk.assign_from_similarities(sk.similarities(corpus, means))
+        return best == 0.0                     # counts cancelling signed objects too
+    return "zero_similarity_objects", zero_similarity_objects
+
+
+def _mut_lockstep_inverted_exclusion(orig):
+    return "lockstep_check", _lockstep_with("inverted_exclusion")
+
+
+def _mut_lockstep_unindexed_rows(orig):
+    return "lockstep_check", _lockstep_with("unindexed")
+
+
+def _mut_lockstep_best_tol_ignored(orig):
+    return "lockstep_check", _lockstep_with("best_tol_ignored")
+
+
 MUTANTS = [_mut_drop_last_term, _mut_highest_id_ties, _mut_no_normalisation, _mut_shifted_cluster,
            _mut_reversed_means, _mut_gap_sign, _mut_empty_loses_mean, _mut_shifted_object,
-           _mut_negated_similarity, _mut_count_per_term_not_per_entry, _mut_no_update]
+           _mut_negated_similarity, _mut_count_per_term_not_per_entry, _mut_no_update,
+           _mut_lockstep_inverted_exclusion, _mut_lockstep_unindexed_rows, _mut_lockstep_best_tol_ignored,
+           _mut_zero_sim_by_best_value]
 
 
 @pytest.mark.parametrize("mutant", MUTANTS, ids=[m.__name__ for m in MUTANTS])
@@ -370,5 +511,7 @@ def name_of(mutant):
         _mut_reversed_means: "similarities", _mut_gap_sign: "assign_from_similarities",
         _mut_empty_loses_mean: "update", _mut_shifted_object: "cluster_sums",
         _mut_negated_similarity: "similarities", _mut_count_per_term_not_per_entry: "multiplication_count",
-        _mut_no_update: "update",
+        _mut_no_update: "update", _mut_lockstep_inverted_exclusion: "lockstep_check",
+        _mut_lockstep_unindexed_rows: "lockstep_check", _mut_lockstep_best_tol_ignored: "lockstep_check",
+        _mut_zero_sim_by_best_value: "zero_similarity_objects",
     }[mutant]
