@@ -108,7 +108,8 @@ typedef struct {
                               (all N on the first assignment) */
   int64_t entries_visited; /* posting entries multiplied: sum_i sum_h (nc)_{t_(i,h)}, Eq. 15 */
   int64_t ivf_entries;     /* E = sum_p (nc)_p, tuples in the inverted file used */
-  int64_t n_zero_sim;      /* objects whose best similarity is exactly 0 */
+  int64_t n_zero_sim;      /* objects that share no term with any mean (they meet no posting
+                              entry; Algorithm 3 never assigns them, here they go to cluster 0) */
   int64_t n_flagged;       /* objects whose FP32 top-2 gap was within the error bound */
   int64_t n_rescored;      /* objects re-scored in FP64 */
   double objective;        /* J = sum_i rho(x_i, mu_a(i)), Eq. 5, FP64 accumulation */
@@ -200,6 +201,17 @@ ivf_status ivf_iterate(ivf_ctx* ctx, int32_t max_iter, int32_t* iters_done, int3
 ivf_status ivf_get_assign(ivf_ctx* ctx, int32_t* out);        /* int32[N] */
 ivf_status ivf_get_best(ivf_ctx* ctx, float* out);            /* float[N] */
 ivf_status ivf_get_gap(ivf_ctx* ctx, float* out);             /* float[N] */
+/* Per-result error statement of the last assignment: out[i] >= |best_i - rho_i|
+ * where best_i is the returned best similarity and rho_i the exact similarity
+ * of object i to its returned cluster under the FP64 master means.  For an
+ * object scored in FP32 accumulation it is the bound E_i that decides the
+ * re-score (FP32 storage: mean rounding plus FMA recursive summation over the
+ * object's m terms; FP16/BF16: both operands' rounding, the FP16 subnormal
+ * floor and the same summation term; relative to best_i when every object
+ * and mean value is >= 0, else scaled by ||x_i||); for an object re-scored
+ * in FP64 it is the FP64 summation error plus the rounding of best_i to
+ * float; 0 for an object that met no posting entry.  float[N]. */
+ivf_status ivf_get_err_bound(ivf_ctx* ctx, float* out);
 ivf_status ivf_get_info(ivf_ctx* ctx, ivf_info* out);         /* host */
 /* FP64 master means, cluster-major: ptr int64[K+1], term int32[E], val double[E];
  * any of the three may be NULL. */

@@ -230,7 +230,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
   float acc[RR];
   const int cmask = a.tiled ? (a.k_tile - 1) : 0xFFFF;
   const unsigned lt = (1u << lane) - 1u;
-  unsigned long long my_entries = 0;
+  unsigned long long my_entries = 0, my_zero = 0;
   const bool nonneg = a.nonneg != 0 && (a.negative == nullptr || *a.negative == 0u) &&
                       (a.means_negative == nullptr || *a.means_negative == 0u);
 
@@ -540,15 +540,17 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
     }
 
     const float g = best - second;
-    if (lane == 0) {
-      a.assign[i] = bid;
-      a.best[i] = best;
-      a.gap[i] = g;
-    }
     // An object that met no posting entry has rho = 0 exactly for every
     // cluster: its lowest-id argmax is exact and needs no re-score.
     const bool any_entry = __any_sync(IVF_FULL_MASK, my_entries != entries_before);
     const float e2 = bound.e2(best);
+    if (lane == 0) {
+      a.assign[i] = bid;
+      a.best[i] = best;
+      a.gap[i] = g;
+      if (a.err != nullptr) a.err[i] = any_entry ? 0.5f * e2 : 0.f;
+      if (!any_entry) ++my_zero;
+    }
     if (a.rescore && any_entry && g <= e2) {
       prune_candidates(cand_id, cand_val, ncand, best - e2, lane);
       unsigned slot = 0;
@@ -567,6 +569,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) my_entries += __shfl_xor_sync(IVF_FULL_MASK, my_entries, o);
   if (lane == 0 && my_entries) atomicAdd(a.entries, my_entries);
+  if (lane == 0 && my_zero && a.n_zero_sim != nullptr) atomicAdd(a.n_zero_sim, my_zero);
 }
 
 // ------------------------------------------------------------- re-score
@@ -632,9 +635,15 @@ __global__ void __launch_bounds__(256) k_rescore(const RescoreArgs a) {
       top2_push_d(best, bid, second, acc, c);
     }
     if (lane == 0) {
+      const float bf = __double2float_rn(best);
       a.assign[i] = bid;
-      a.best[i] = __double2float_rn(best);
+      a.best[i] = bf;
       a.gap[i] = __double2float_rn(best - second);
+      // FP64 recursive summation of at most m products (each |v u| summing
+      // to <= ||x||): (m + 1) 2^-53 ||x||, then the rounding to FP32
+      if (a.err != nullptr)
+        a.err[i] = fabsf(bf) * 5.9604645e-08f + (float)((double)(r1 - r0 + 1) * 1.1102230246251565e-16 *
+                                                        (double)a.nx[i]) + 1e-30f;
       atomicAdd(a.n_rescored, 1ull);
     }
   }
@@ -646,12 +655,11 @@ constexpr int RED_THREADS = 256;
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs a) {
   double obj = 0.0;
-  unsigned long long ch = 0, zs = 0;
+  unsigned long long ch = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_docs; i += stride) {
     const float bst = a.best[i];
     obj += (double)bst;
-    zs += (bst == 0.f) ? 1ull : 0ull;
     const bool changed = a.prev == nullptr || a.assign[i] != a.prev[i];
     if (changed) {
       ++ch;
@@ -661,46 +669,41 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs a) {
     }
   }
   __shared__ double so[RED_THREADS / 32];
-  __shared__ unsigned long long sc[RED_THREADS / 32], sz[RED_THREADS / 32];
+  __shared__ unsigned long long sc[RED_THREADS / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     obj += __shfl_down_sync(IVF_FULL_MASK, obj, o);
     ch += __shfl_down_sync(IVF_FULL_MASK, ch, o);
-    zs += __shfl_down_sync(IVF_FULL_MASK, zs, o);
   }
   if (lane == 0) {
     so[warp] = obj;
     sc[warp] = ch;
-    sz[warp] = zs;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    unsigned long long c = 0, z = 0;
+    unsigned long long c = 0;
     for (int w2 = 0; w2 < RED_THREADS / 32; ++w2) {
       t += so[w2];
       c += sc[w2];
-      z += sz[w2];
     }
     a.part_obj[blockIdx.x] = t;
     a.part_cnt[2 * blockIdx.x] = c;
-    a.part_cnt[2 * blockIdx.x + 1] = z;
   }
 }
 
 __global__ void k_reduce_final(const ReduceArgs a, int nblocks) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double t = 0.0;
-  unsigned long long c = 0, z = 0;
+  unsigned long long c = 0;
   for (int b = 0; b < nblocks; ++b) {
     t += a.part_obj[b];
     c += a.part_cnt[2 * b];
-    z += a.part_cnt[2 * b + 1];
   }
   a.out_obj[0] = t;
   a.out_cnt[0] = c;
-  a.out_cnt[1] = z;
+  a.out_cnt[1] = a.zero_sim != nullptr ? a.zero_sim[0] : 0ull;
   if (a.n_inst == 1) a.inst_changed[0] = (long long)c;
   a.acc_entries[0] += a.entries[0];
   a.acc_rescored[0] += a.n_rescored[0];

@@ -36,6 +36,7 @@ struct DevCounters {
   unsigned long long entries;
   unsigned long long n_rescored;
   unsigned long long work_cls[4];   // work counters of the per-class launches (batched contexts)
+  unsigned long long zero_sim;      // objects that met no posting entry in the last assignment
   unsigned int n_flagged;
   unsigned int status;
   double objective;
@@ -145,6 +146,7 @@ struct ivf_ctx {
   bool has_prev_for_next = false;
   float* best = nullptr;
   float* gap = nullptr;
+  float* errb = nullptr;  // per object: bound on |best - rho_FP64|
   int32_t* flag_obj = nullptr;
   int32_t* flag_cnt = nullptr;
   int32_t* flag_cand = nullptr;
@@ -441,6 +443,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   for (int b = 0; b < 2; ++b) AL(c->assign[b], N);
   AL(c->best, N);
   AL(c->gap, N);
+  AL(c->errb, N);
   AL(c->flag_obj, N);
   AL(c->flag_cnt, N);
   c->cand_slots = std::min<int64_t>(N, int64_t(1) << 20);
@@ -715,8 +718,10 @@ AssignArgs assign_args(ivf_ctx* c, const Shape& sh, int target, int rescore) {
   a.assign = c->assign[target];
   a.best = c->best;
   a.gap = c->gap;
+  a.err = c->errb;
   a.work = &c->dc->work;
   a.entries = &c->dc->entries;
+  a.n_zero_sim = &c->dc->zero_sim;
   a.n_flagged = &c->dc->n_flagged;
   a.flag_obj = c->flag_obj;
   a.flag_cnt = c->flag_cnt;
@@ -1166,6 +1171,8 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
     r.assign = c->assign[target];
     r.best = c->best;
     r.gap = c->gap;
+    r.err = c->errb;
+    r.nx = c->nx;
     r.n_rescored = &c->dc->n_rescored;
     CK(c, launch_rescore(r, 2 * c->num_sms, s));
   }
@@ -1181,6 +1188,7 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
   ra.part_cnt = c->part_cnt;
   ra.out_obj = &c->dc->objective;
   ra.out_cnt = c->dc->cnt;
+  ra.zero_sim = &c->dc->zero_sim;
   ra.entries = &c->dc->entries;
   ra.n_rescored = &c->dc->n_rescored;
   ra.acc_entries = &c->dc->acc_entries;
@@ -1688,6 +1696,14 @@ ivf_status ivf_get_gap(ivf_ctx* c, float* out) {
   if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
   if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment yet");
   CK(c, cudaMemcpyAsync(out, c->gap, sizeof(float) * c->N, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_get_err_bound(ivf_ctx* c, float* out) {
+  if (!c || !out) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment yet");
+  CK(c, cudaMemcpyAsync(out, c->errb, sizeof(float) * c->N, cudaMemcpyDefault, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));
   return IVF_OK;
 }

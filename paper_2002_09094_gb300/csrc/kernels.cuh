@@ -50,8 +50,10 @@ struct AssignArgs {
   int32_t* assign;           // [N]
   float* best;               // [N]
   float* gap;                // [N]
+  float* err = nullptr;      // [N] or null: bound on |best - rho_FP64| of the returned best
   unsigned long long* work;     // object counter, zero before launch
   unsigned long long* entries;  // visited posting entries (accumulated)
+  unsigned long long* n_zero_sim = nullptr;  // objects that met no posting entry (accumulated), or null
   unsigned int* n_flagged;      // flagged objects (accumulated from 0)
   int32_t* flag_obj;            // [N]
   int32_t* flag_cnt;            // [N] candidates, -1 = overflow (all clusters)
@@ -113,6 +115,8 @@ struct RescoreArgs {
   int32_t* assign;
   float* best;
   float* gap;
+  float* err;            // [N] or null: bound of the re-scored best
+  const float* nx;       // [N] object norms, rounded up (needed with err)
   unsigned long long* n_rescored;
 };
 cudaError_t launch_rescore(const RescoreArgs& a, int blocks, cudaStream_t s);
@@ -129,6 +133,7 @@ struct ReduceArgs {
   unsigned long long* part_cnt;  // [2 * blocks]: changed, zero-sim
   double* out_obj;          // [1]
   unsigned long long* out_cnt;   // [2]
+  const unsigned long long* zero_sim;  // objects that met no posting entry (from the assignment)
   // window accumulators (added to by the final reduction)
   const unsigned long long* entries;
   const unsigned long long* n_rescored;

@@ -34,7 +34,7 @@ KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG
 # Every symbol include/ivf.h declares.
 EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_from_docs", "ivf_assign",
            "ivf_update", "ivf_iterate", "ivf_get_assign", "ivf_get_best", "ivf_get_gap", "ivf_get_info",
-           "ivf_get_means", "ivf_get_inverted_file", "ivf_get_members", "ivf_set_assign", "ivf_restore_means",
+           "ivf_get_err_bound", "ivf_get_means", "ivf_get_inverted_file", "ivf_get_members", "ivf_set_assign", "ivf_restore_means",
            "ivf_last_error", "ivf_destroy", "ivf_launch_count", "ivf_version", "ivfb_create", "ivfb_get_changed",
            "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static"]
 IVF_STATIC_MAX_DOCS = 16384
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ivf_get_assign": ([vp, vp], st),
         "ivf_get_best": ([vp, vp], st),
         "ivf_get_gap": ([vp, vp], st),
+        "ivf_get_err_bound": ([vp, vp], st),
         "ivf_get_info": ([vp, P(Info)], st),
         "ivf_get_means": ([vp, vp, vp, vp], st),
         "ivf_get_inverted_file": ([vp, vp, vp, vp], st),
@@ -309,6 +310,12 @@ class IVF:
     def get_gap(self) -> np.ndarray:
         a = np.empty(self.n_docs, dtype=np.float32)
         self._check(self._lib.ivf_get_gap(self._ctx, a.ctypes.data))
+        return a
+
+    def get_err_bound(self) -> np.ndarray:
+        """Per object: a bound on |best - rho| against the FP64 means (ivf_get_err_bound)."""
+        a = np.empty(self.n_docs, dtype=np.float32)
+        self._check(self._lib.ivf_get_err_bound(self._ctx, a.ctypes.data))
         return a
 
     def info(self) -> dict:

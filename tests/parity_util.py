@@ -4,7 +4,11 @@ At iteration r the oracle takes the GPU's previous assignment, forms its own
 FP64 means from it, and checks that the GPU's assignment equals the FP64
 argmax for every object whose FP64 top-2 gap is at least 1e-6, that the
 GPU's best similarity is within 1e-5 of the FP64 one, and that the GPU's FP64
-master means equal the oracle's.
+master means equal the oracle's.  Each checked object's best is also held
+to the library's own per-result error statement (ivf_get_err_bound):
+|best_i - rho_i| <= E_i, with rho_i the FP64 similarity to the returned
+cluster, and the count of objects sharing no term with any mean is compared
+with the oracle's.
 """
 from __future__ import annotations
 
@@ -46,6 +50,7 @@ def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, means_rows
         for r in range(1, iters + 1):
             st = m.assign()
             a, b, g = m.get_assign(), m.get_best(), m.get_gap()
+            e = m.get_err_bound()
             sample = rows
             if rows is not None:  # sampled objects plus every object the GPU flagged as a near-tie
                 flagged = np.flatnonzero(g <= 1e-3)
@@ -61,6 +66,8 @@ def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, means_rows
             rep["gpu_assign"] = a
             rep["gpu_best"] = b
             rep["gpu_gap"] = g
+            rep["n_zero_sim_expected"] = int(np.count_nonzero(sk.zero_similarity_objects(corpus, means)))
+            rep.update(err_bound_report(corpus, means, rep, sample, a, b, e))
             m.update()
             new, norm, sizes = sk.update(corpus, a, means, empty_policy)
             rep["means"] = means_report(m.get_means(), new)
@@ -73,8 +80,32 @@ def lockstep(corpus, k, doc_ids, iters, rows=None, best_tol=BEST_TOL, means_rows
         m.close()
 
 
+def err_bound_report(corpus, means, rep, rows, gpu_assign, gpu_best, gpu_err) -> dict:
+    """|best_i - rho_i(a_i)| against the GPU's stated bound E_i on the checked
+    rows, rho in FP64 for the cluster the GPU returned (which differs from the
+    oracle's only for excluded near-ties)."""
+    rows = np.arange(corpus.n_docs) if rows is None else np.asarray(rows, dtype=np.int64)
+    oa = rep["oracle_assign"]
+    rho_gpu_cluster = np.array(rep["oracle_best"], dtype=np.float64)
+    ga = np.asarray(gpu_assign)[rows]
+    diff = np.flatnonzero(ga != oa)
+    if diff.size:
+        rho = sk.similarities(corpus, means, rows[diff])
+        rho_gpu_cluster[diff] = rho[np.arange(diff.size), ga[diff]]
+    err = np.abs(np.asarray(gpu_best, np.float64)[rows] - rho_gpu_cluster)
+    bound = np.asarray(gpu_err, np.float64)[rows]
+    ratio = err / np.maximum(bound, 1e-30)
+    return {"err_within_bound": bool(np.all(err <= bound + 1e-12)),
+            "max_err_over_bound": float(ratio.max()) if rows.size else 0.0,
+            "max_abs_err": float(err.max()) if rows.size else 0.0,
+            "max_bound": float(bound.max()) if rows.size else 0.0}
+
+
 def assert_report_ok(rep, check_best=True, check_means=True, check_objective=True):
     assert rep["mismatches"] == 0, (rep["r"], rep["mismatches"], rep["mismatch_rows"])
+    assert rep["err_within_bound"], (rep["r"], rep["max_err_over_bound"], rep["max_abs_err"])
+    assert rep["stats"]["n_zero_sim"] == rep["n_zero_sim_expected"], (rep["stats"]["n_zero_sim"],
+                                                                       rep["n_zero_sim_expected"])
     if check_best:
         assert rep["best_ok"], (rep["r"], rep["max_best_err"])
     st = rep["stats"]

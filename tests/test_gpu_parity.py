@@ -225,6 +225,20 @@ def test_zero_similarity_objects_and_empty_rows():
     assert st["n_zero_sim"] == 3
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_zero_similarity_counts_objects_without_entries(storage):
+    """Signed values: object 0 shares both terms with mean 0 = (1, -1)/sqrt(2)
+    and 0.5 a - 0.5 a cancels exactly, while mean 1 gives -0.5, so its best is
+    0 although it met posting entries; it is not counted.  Objects 1 (a term
+    no mean has) and 2 (no terms) are."""
+    c = dg.corpus_from_rows([([0, 1], [0.5, 0.5]), ([5], [1.0]), ([], [])], 6)
+    rows = (np.array([0, 2, 3], np.int64), np.array([0, 1, 0], np.int32), np.array([1.0, -1.0, -1.0], np.float32))
+    reps = lockstep(c, 2, None, 2, means_rows=rows, storage=storage)
+    for rep in reps:
+        assert_report_ok(rep)
+    assert reps[0]["gpu_best"][0] == 0.0 and reps[0]["stats"]["n_zero_sim"] == 2
+
+
 @pytest.mark.parametrize("n", [1, 2, 33, 1000])
 def test_ragged_tiny_collections(n):
     c = corpus_for(n, 64, mean_len=5.0, seed=n, lo=1, hi=20)
