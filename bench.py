@@ -53,8 +53,16 @@ def parse():
     p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
     p.add_argument("--e2e-steps", type=int, default=0,
                    help="steps of the end-to-end leg (0 = as many as --steps)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle timing sample")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle timing sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--schedule", choices=["auto", "tile_major", "object_major"], default="auto",
+                   help="assignment schedule (auto = the autotuner picks)")
+    p.add_argument("--no-mixed", action="store_true", help="skip the FP16/BF16 arms of the FP32 line")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched sub-line")
+    p.add_argument("--batched-instances", type=int, default=32,
+                   help="instances of the batched sub-line of the default line (0 = none)")
+    p.add_argument("--batched-steps", type=int, default=8, help="timed iterations of the batched sub-line")
+    p.add_argument("--fp64-sample", type=int, default=2000, help="objects checked against the FP64 oracle")
     return p.parse_args()
 
 
@@ -79,10 +87,12 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_per_launch(workload_name: str, storage: str):
-    """DRAM bytes per assignment launch from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken or the
-    counters are for another workload."""
+def traffic_per_launch(workload_name: str, storage: str, schedule: str | None = None, what: str = "bytes"):
+    """DRAM bytes (what="bytes") or L2 bytes (what="l2_bytes") per assignment
+    step from the committed ncu summary, or None when the kernel source
+    changed since the counters were taken, the counters are for another
+    workload, or they were taken under another schedule (tile-major or
+    object-major) than the one in use."""
     try:
         text = open(TRAFFIC_FILE).read()
     except OSError:
@@ -94,7 +104,10 @@ def traffic_per_launch(workload_name: str, storage: str):
     m_w = re.search(r"^workload:\s*(\S+)", text, re.M)
     if not m_w or m_w.group(1) != workload_name:
         return None
-    m = re.search(rf"bytes_per_launch\[{storage}\]:\s*([0-9.eE+]+)", text)
+    m_s = re.search(rf"^schedule\[{storage}\]:\s*(\S+)", text, re.M)
+    if m_s and schedule is not None and m_s.group(1) != schedule:
+        return None
+    m = re.search(rf"^{what}_per_launch\[{storage}\]:\s*([0-9.eE+]+)", text, re.M)
     return float(m.group(1)) if m else None
 
 
@@ -292,6 +305,122 @@ def run_reference(args, rank, world):
           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
 
 
+def assign_roofline(c, w, storage, timing, info, l2_gbs, schedule):
+    """Roofline of the assignment step (every launch of one step: one per
+    cluster tile when tile-major, plus the pass over near-ties).
+
+    achieved = algorithmic bytes (the CSR once, Eq. 15's posting entries at
+    id + value bytes each, the outputs) / the step's kernel time.  Those
+    bytes are served mostly by L2 (the hot lists stay resident), so the bound
+    reported is L2, against the read bandwidth of a resident set measured live
+    on this GPU (ivf_probe_l2_read).  Beside it: the DRAM bytes ncu counted
+    for the same step (committed summary) as a fraction of the measured HBM
+    peak, and the algorithmic bytes against HBM ("effective", above 1 when L2
+    reuse is high)."""
+    bv = 4 if storage == "f32" else 2
+    n_steps = max(1, timing["n_assign"])
+    kern_ms = timing["assign_kernel_ms"] / n_steps
+    entries = timing["entries_visited"] / n_steps
+    b_assign = c.nnz * (4 + bv) + 8 * (c.n_docs + 1) + entries * (2 + bv) + c.n_docs * 12
+    hbm, hbm_kind = peaks()
+    achieved = b_assign / (kern_ms / 1e3) / 1e9
+    traffic = traffic_per_launch(w.name, storage, schedule)
+    l2_bytes = traffic_per_launch(w.name, storage, schedule, what="l2_bytes")
+    dram_gbs = traffic / (kern_ms / 1e3) / 1e9 if traffic else None
+    return {"bound": "l2", "achieved": round(achieved, 1), "peak": round(l2_gbs, 1), "unit": "GB/s",
+            "frac": round(achieved / l2_gbs, 4), "traffic": traffic,
+            "peak_source": "L2 read bandwidth of a resident set, measured live on this GPU by ivf_probe_l2_read "
+                           "(builder-measured; not a driver peak)",
+            "kernel": ("assign step: k_build_xhead + cuBLAS GEMM + k_assign" if info["dense_head_tensor"]
+                       else "assign step: k_assign (%s)" % schedule),
+            "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
+            "kernel_ms": round(kern_ms, 4),
+            "l2_bytes_ncu": l2_bytes,
+            "hbm": {"achieved": round(dram_gbs, 1) if dram_gbs else None, "peak": hbm, "unit": "GB/s",
+                    "frac": round(dram_gbs / hbm, 4) if dram_gbs else None,
+                    "peak_source": f"{hbm_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                    "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of the step's launches"},
+            "effective_vs_hbm": {"achieved": round(achieved, 1), "peak": hbm, "frac": round(achieved / hbm, 4),
+                                 "label": "effective (L2 reuse): algorithmic bytes against HBM"}}
+
+
+def mixed_arm(c, w, ids, storage, args, stream, cycles_total, a32_final):
+    """FP16/BF16 storage on the same data and initial means: device-timed
+    iterations, then as many assignments in all as the FP32 arm made, and its
+    final assignment compared with the FP32 one object by object."""
+    import torch
+
+    from paper_2002_09094_gb300 import ivf
+
+    with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=storage, stream=stream.cuda_stream) as m:
+        m.set_means_from_docs(ids)
+        for _ in range(args.warmup):
+            m.assign(stats=False)
+            m.update()
+        torch.cuda.synchronize()
+        m.timing_reset(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            m.assign(stats=False)
+            m.update()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        timing = m.get_timing()
+        m.timing_reset(False)
+        info = m.info()
+        done = args.warmup + args.steps
+        st = None
+        while done < cycles_total:
+            st = m.assign()
+            done += 1
+            if done < cycles_total:
+                m.update()
+        a = m.get_assign()
+        err = m.get_err_bound()
+    n_steps = max(1, timing["n_assign"])
+    return {"storage": storage, "value": ms / 1e3, "unit": UNIT, "ms_per_step": round(ms, 4),
+            "phases_ms_per_step": {"assign_kernel": round(timing["assign_kernel_ms"] / n_steps, 4),
+                                   "assign_step": round(timing["assign_step_ms"] / n_steps, 4),
+                                   "update": round(timing["update_ms"] / max(1, timing["n_update"]), 4)},
+            "rescored_per_step": round(timing["n_rescored"] / n_steps, 1),
+            "kernel": kernel_desc(info),
+            "assignments_vs_f32": {"assignments": cycles_total,
+                                   "objects_differing": int(np.count_nonzero(a != a32_final)),
+                                   "flagged_last": int(st["n_flagged"]) if st else None,
+                                   "rescored_last": int(st["n_rescored"]) if st else None},
+            "err_bound_last": {"max": float(err.max()), "median": float(np.median(err))}}
+
+
+def kernel_desc(info):
+    if not info["dense_head_r"]:
+        return "sparse" + (" tile-major" if info.get("tile_major") else "")
+    return "%s r=%d sub=%d theta=%.2f rows=%d%s" % (
+        "tensor_head" if info["dense_head_tensor"] else "dense_head", info["dense_head_r"], info["dense_head_sub"],
+        info["dense_head_theta"], info["dense_head_rows"], " tile-major" if info.get("tile_major") else "")
+
+
+def fp64_sample_check(c, means, gpu_assign, gpu_best, gpu_err, rows):
+    """Oracle similarities on a row sample (the CPU-baseline leg's sample):
+    objects whose assignment differs from the FP64 argmax (gap >= 1e-6), and
+    the measured |best - rho_FP64| against the GPU's per-object bound."""
+    import oracle.spherical_kmeans as sk
+
+    rho = sk.similarities(c, means, rows)
+    a, best, gap = sk.assign_from_similarities(rho)
+    ga = gpu_assign[rows]
+    rho_g = rho[np.arange(len(rows)), ga]
+    err = np.abs(gpu_best[rows].astype(np.float64) - rho_g)
+    bound = gpu_err[rows].astype(np.float64)
+    clear = gap >= 1e-6
+    return {"objects": int(len(rows)), "assign_equal_fp64": int(np.count_nonzero((ga == a) & clear)),
+            "excluded_near_ties": int(np.count_nonzero(~clear)),
+            "differing": int(np.count_nonzero((ga != a) & clear)),
+            "max_abs_err": float(err.max()), "max_err_over_bound": float((err / np.maximum(bound, 1e-30)).max()),
+            "all_within_bound": bool(np.all(err <= bound + 1e-12))}
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -320,9 +449,10 @@ def run_ours(args, rank, world, local):
     ids = dg.init_doc_ids(c.n_docs, w.k, w.init_seed)
     stream = torch.cuda.Stream()
     bv = 4 if args.storage == "f32" else 2
+    l2_gbs = ivf.probe_l2_read_gbs(stream=stream.cuda_stream)
     with torch.cuda.stream(stream):
         m = ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage, stream=stream.cuda_stream,
-                    kernel=args.kernel)
+                    kernel=args.kernel, schedule=args.schedule)
         m.set_means_from_docs(ids)
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
@@ -395,38 +525,25 @@ def run_ours(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1) / n_e2e
-        # current state for the CPU baseline sample
+        cycles_total = args.warmup + args.steps + 1 + n_e2e
+        # the state of the last assignment: the means it used are the ones
+        # before its update, so the FP64 check below re-runs that assignment
         means_np = m.get_means()
-        assign_np = m.get_assign()
+        st_last = m.assign()
+        assign_np, best_np, err_np = m.get_assign(), m.get_best(), m.get_err_bound()
         m.close()
-        # mixed precision is compared with FP32 at equal assignments: the
-        # same number of iterations from the same initial means in FP32
-        equal_f32 = None
-        if args.storage != "f32":
-            cycles = args.warmup + args.steps + n_e2e + 1
-            with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage="f32",
-                         stream=stream.cuda_stream) as m32:
-                m32.set_means_from_docs(ids)
-                for q in range(cycles):
-                    m32.assign(stats=False)
-                    if q + 1 < cycles:
-                        m32.update()
-                a32 = m32.get_assign()
-            equal_f32 = {"iterations": cycles, "objects_differing": int(np.count_nonzero(a32 != assign_np))}
+        mixed = []
+        if args.storage == "f32" and not args.no_mixed:
+            for st in ("bf16", "f16"):
+                mixed.append(mixed_arm(c, w, ids, st, args, stream, cycles_total + 1, assign_np))
+        batched = None
+        if not args.no_batched and args.batched_instances > 0:
+            batched = measure_batched(args, args.batched_instances, stream)
 
     ms_per_step = total_ms / args.steps
     n_steps = max(1, timing["n_assign"])
-    kern_ms = timing["assign_kernel_ms"] / n_steps
-    entries = timing["entries_visited"] / n_steps
-    b_assign = c.nnz * (4 + bv) + 8 * (c.n_docs + 1) + entries * (2 + bv) + c.n_docs * 12
-    peak, peak_kind = peaks()
-    achieved = b_assign / (kern_ms / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic_per_launch(w.name, args.storage),
-            "kernel": ("assign step: k_build_xhead + cuBLAS GEMM + k_assign" if info["dense_head_tensor"]
-                       else "k_assign"), "peak_source": f"{peak_kind} hbm_gbs",
-            "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
-            "kernel_ms": round(kern_ms, 4)}
+    schedule = "tile_major" if info.get("tile_major") else "object_major"
+    roof = assign_roofline(c, w, args.storage, timing, info, l2_gbs, schedule)
     out = {"metric": METRIC, "value": ms_per_step / 1e3 / world, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": args.storage,
@@ -435,22 +552,27 @@ def run_ours(args, rank, world, local):
                       "storage": args.storage, "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2 (CSR %.2f GB); no flush" % (c.nnz * 8 / 1e9),
                       "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"],
-                      "kernel": ("%s r=%d sub=%d theta=%.2f rows=%d" % (
-                          "tensor_head" if info["dense_head_tensor"] else "dense_head",
-                          info["dense_head_r"], info["dense_head_sub"], info["dense_head_theta"],
-                          info["dense_head_rows"])) if info["dense_head_r"] else "sparse",
+                      "kernel": kernel_desc(info), "schedule": schedule,
                       "ivf_entries": info["ivf_entries"], "generation_s": round(gen_s, 1)},
            "step_ms": {"min": round(min(step_ms), 3), "median": round(statistics.median(step_ms), 3),
                        "max": round(max(step_ms), 3)},
-           "phases_ms_per_step": {"assign_kernel": round(kern_ms, 4),
+           "phases_ms_per_step": {"assign_kernel": round(timing["assign_kernel_ms"] / n_steps, 4),
                                   "assign_step": round(timing["assign_step_ms"] / n_steps, 4),
                                   "update": round(timing["update_ms"] / max(1, timing["n_update"]), 4)},
+           "rescored_per_step": round(timing["n_rescored"] / n_steps, 1),
            "roofline": roof,
            "e2e": {"value": e2e_ms / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h), "steps": n_e2e},
-           "gpu_launches": int(launches), "clocks": clk}
-    if equal_f32 is not None:
-        out["assignments_vs_f32"] = equal_f32
+           "gpu_launches": int(launches), "clocks": clk,
+           "err_bound_last": {"max": float(err_np.max()), "median": float(np.median(err_np)),
+                              "flagged": int(st_last["n_flagged"]), "rescored": int(st_last["n_rescored"])}}
+    if mixed:
+        out["mixed_precision"] = {
+            "note": "same data and initial means; value = device-timed s/iter; assignments compared with the "
+                    "FP32 arm after the same number of assignments",
+            **{a["storage"]: {**a, "speedup_vs_f32": round(ms_per_step / a["ms_per_step"], 3)} for a in mixed}}
+    if batched is not None:
+        out["batched"] = batched
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle.spherical_kmeans as sk
 
@@ -459,6 +581,10 @@ def run_ours(args, rank, world, local):
         v, desc = oracle_iteration_sample(c, means, assign_np, np.random.default_rng(1), args.cpu_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                "sample": desc + "; means = the GPU's current FP64 means"}
+        # the last assignment against the FP64 argmax on a sample, and the
+        # measured error of each best against the GPU's own per-object bound
+        rows = np.random.default_rng(3).choice(c.n_docs, size=min(c.n_docs, args.fp64_sample), replace=False)
+        out["fp64_check"] = fp64_sample_check(c, means, assign_np, best_np, err_np, np.sort(rows))
         # the paper's own method on the same host, one thread (as the paper
         # runs it) and every core
         pm = {}
@@ -473,19 +599,17 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
-def run_batched(args, rank, world, local):
-    """Many independent instances of uneven N, K and D in one context: one
-    launch per phase for all of them and CUDA-graph iterations, against the
-    same instances run one after the other in their own contexts."""
+def measure_batched(args, n_instances, stream):
+    """Many independent instances of uneven N, K and D in one context (one
+    launch per phase for all of them, CUDA-graph iterations) against the same
+    instances run one after the other in their own contexts.  Returns the
+    batched line's fields."""
     import torch
 
-    from paper_2002_09094_gb300 import build as cuda_build
     from paper_2002_09094_gb300 import datagen as dg
     from paper_2002_09094_gb300 import ivf
 
-    cuda_build.build()
-    torch.cuda.set_device(local)
-    ws = dg.batched_workloads(n_instances=args.instances)
+    ws = dg.batched_workloads(n_instances=n_instances)
     t0 = time.time()
     cs = [dg.make_corpus(w.corpus) for w in ws]
     gen_s = time.time() - t0
@@ -495,11 +619,11 @@ def run_batched(args, rank, world, local):
     row_ptr = np.concatenate([c.row_ptr[:-1] + o for c, o in zip(cs, offs)] + [offs[-1:]]).astype(np.int64)
     term = np.concatenate([c.term for c in cs])
     val = np.concatenate([c.val for c in cs])
-    iters = args.steps
-    stream = torch.cuda.Stream()
+    iters = args.batched_steps
+    storage = "f32"
     with torch.cuda.stream(stream):
         m = ivf.BatchedIVF(row_ptr, term, val, inst_docs, [c.n_terms for c in cs], [w.k for w in ws],
-                           storage=args.storage, stream=stream.cuda_stream)
+                           storage=storage, stream=stream.cuda_stream)
         del term, val
         m.set_means_from_docs(np.concatenate(ids))
         clocks = ClockSampler(torch.cuda.current_device())
@@ -531,7 +655,7 @@ def run_batched(args, rank, world, local):
         seq_ph = {"assign_kernel": 0.0, "assign_step": 0.0, "update": 0.0}
         equal = True
         for b, (w, c, d) in enumerate(zip(ws, cs, ids)):
-            with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=args.storage,
+            with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, w.k, storage=storage,
                          stream=stream.cuda_stream) as s1:
                 s1.set_means_from_docs(d)
                 s1.iterate(args.warmup)
@@ -551,35 +675,38 @@ def run_batched(args, rank, world, local):
                 s1.timing_reset(False)
                 for key in seq_ph:
                     seq_ph[key] += t1[key + "_ms"]
-    # roofline of the assignment launches of the eager iteration (all classes)
-    bv = 4 if args.storage == "f32" else 2
     n_all, nnz_all = int(inst_docs[-1]), int(offs[-1])
-    b_assign = nnz_all * (4 + bv) + 8 * (n_all + 1) + int(tph["entries_visited"]) * (2 + bv) + n_all * 12
-    peak, peak_kind = peaks()
-    achieved = b_assign / (tph["assign_kernel_ms"] / 1e3) / 1e9
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "kernel": "k_assign (one launch per class)",
-            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": int(b_assign),
-            "entries_per_launch": int(tph["entries_visited"]), "kernel_ms": round(tph["assign_kernel_ms"], 4)}
-    out = {"metric": METRIC, "value": batched_ms / 1e3, "unit": UNIT, "n_gpus": world, "steps": int(done),
-           "warmup": args.warmup, "ms_per_step": round(batched_ms, 4), "higher_is_better": False,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "f32" else args.storage,
-           "data": "synthetic", "impl": "ours",
-           "config": {"workload": f"batched-{args.instances}-instances", "instances": args.instances,
-                      "n_docs": int(inst_docs[-1]), "nnz": int(offs[-1]), "k_total": int(sum(w.k for w in ws)),
-                      "storage": args.storage, "iterations": "graph-captured", "generation_s": round(gen_s, 1),
-                      "k_tile": info["k_tile"], "warps_per_block": info["warps_per_block"]},
-           "phases_ms_one_eager_iteration": {"assign_kernel": round(tph["assign_kernel_ms"], 3),
-                                             "assign_step": round(tph["assign_step_ms"], 3),
-                                             "update": round(tph["update_ms"], 3)},
-           "kernel": ("dense_head r=%d sub=%d theta=%.2f" % (info["dense_head_r"], info["dense_head_sub"],
-                                                             info["dense_head_theta"]))
-           if info["dense_head_r"] else "sparse",
-           "sequential_s_per_iter": seq_ms / 1e3, "batched_speedup": round(seq_ms / batched_ms, 3),
-           "sequential_phases_ms_one_eager_iteration": {k_: round(v_, 3) for k_, v_ in seq_ph.items()},
-           "equal_assignments": equal, "converged": bool(conv), "roofline": roof,
-           # the host-to-device leg is measured on the single-instance line
-           "e2e": None, "gpu_launches": int(launches), "clocks": clk}
+    return {"workload": f"batched-{n_instances}-instances", "instances": n_instances, "n_docs": n_all,
+            "nnz": nnz_all, "k_total": int(sum(w.k for w in ws)), "storage": storage,
+            "value": batched_ms / 1e3, "unit": UNIT, "ms_per_step": round(batched_ms, 4), "steps": int(done),
+            "iterations": "graph-captured", "generation_s": round(gen_s, 1),
+            "phases_ms_one_eager_iteration": {"assign_kernel": round(tph["assign_kernel_ms"], 3),
+                                              "assign_step": round(tph["assign_step_ms"], 3),
+                                              "update": round(tph["update_ms"], 3)},
+            "kernel": kernel_desc(info),
+            "sequential_s_per_iter": seq_ms / 1e3, "batched_speedup": round(seq_ms / batched_ms, 3),
+            "sequential_phases_ms_one_eager_iteration": {k_: round(v_, 3) for k_, v_ in seq_ph.items()},
+            "equal_assignments": equal, "converged": bool(conv), "gpu_launches": int(launches), "clocks": clk,
+            "entries_one_eager_iteration": int(tph["entries_visited"])}
+
+
+def run_batched(args, rank, world, local):
+    """The batched workload as the line's own metric (--workload batched)."""
+    import torch
+
+    from paper_2002_09094_gb300 import build as cuda_build
+
+    cuda_build.build()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    args.batched_steps = args.steps
+    b = measure_batched(args, args.instances, stream)
+    out = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": world, "steps": b["steps"],
+           "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "ours",
+           "config": {k_: b[k_] for k_ in ("workload", "instances", "n_docs", "nnz", "k_total", "storage",
+                                            "iterations", "generation_s", "kernel")},
+           "batched": b, "e2e": None, "gpu_launches": b["gpu_launches"], "clocks": b["clocks"]}
     if rank == 0:
         emit(out)
 

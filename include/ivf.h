@@ -75,6 +75,11 @@ typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
 #define IVF_FLAG_TENSOR_HEAD 16u /* FP16/BF16 storage: autotune only among dense-head kernels whose
                                     head part is a tensor-core GEMM of the objects' dense head
                                     values with the dense rows (cuBLAS), batch by batch */
+#define IVF_FLAG_TILE_MAJOR 32u  /* autotune only among tile-major schedules: one launch per tile of the
+                                    cluster range over all objects, (best, id, second) carried in
+                                    device memory between launches (tiled shapes, one instance) */
+#define IVF_FLAG_OBJECT_MAJOR 64u /* autotune only among object-major schedules (each object walks all
+                                     of its cluster tiles in one launch) */
 
 typedef struct {
   int64_t n_docs;      /* N >= 1 */
@@ -131,6 +136,7 @@ typedef struct {
   int32_t dense_head_tensor; /* 1: the head part is computed by a tensor-core GEMM */
   float dense_head_theta;  /* lists covering >= theta * K clusters are stored densely */
   int64_t dense_head_rows; /* dense rows in the inverted file last built */
+  int32_t tile_major;      /* 1: the assignment runs tile-major (one launch per cluster tile) */
 } ivf_info;
 
 /* Create a context for one clustering problem and copy the objects in.
@@ -254,6 +260,30 @@ typedef struct {
 ivf_status ivf_timing_reset(ivf_ctx* ctx, int32_t enable);
 /* Sums over the window so far; synchronises the stream. */
 ivf_status ivf_get_timing(ivf_ctx* ctx, ivf_timing* out);
+
+/* The tensor-core block of the dense head (the paper's full inverted file
+ * IFN, Section 4, for the terms whose posting lists are dense), on caller
+ * buffers: d[i][c] = sum_{s < k} a[i][s] * b[c][s] for i < m, c < n, with a
+ * (m x k), b (n x k) and d (m x n) row-major DEVICE matrices of 16-bit
+ * values (storage IVF_F16 or IVF_BF16, all three the same type), leading
+ * dimensions lda, ldb, ldd in elements (multiples of 8, pointers 16-byte
+ * aligned), FP32 accumulation on the tensor cores (tcgen05, operands staged
+ * by TMA), d rounded to the 16-bit type.  n must be a multiple of 256 and k
+ * of 64 (IVF_E_INVALID otherwise).  This is the kernel the FP16/BF16
+ * assignment uses for its head part, batch by batch.  Synchronises the
+ * stream; IVF_E_TIMEOUT if a bounded device wait ran out. */
+ivf_status ivf_head_product(int64_t m, int32_t n, int32_t k, const void* a, int64_t lda, const void* b,
+                            int64_t ldb, void* d, int64_t ldd, int32_t storage, void* cuda_stream);
+
+/* Platform probe (no counterpart in the paper): the read bandwidth, in GB/s,
+ * that the current device delivers from a resident set of `bytes` bytes
+ * (>= 1 MiB, a multiple of 16, small enough to stay in L2) read `reps` times
+ * per launch with 16-byte L2-only loads by 4 blocks of 512 threads per SM;
+ * the best of five launches after one warm-up.  The assignment kernel's
+ * posting reads are served mostly by L2, so its bytes per second are
+ * reported against this figure.  Allocates and frees its own buffer;
+ * synchronises the stream. */
+ivf_status ivf_probe_l2_read(int64_t bytes, int32_t reps, void* cuda_stream, double* gbs_out);
 
 /* Number of kernels this library has launched in the process so far (its
  * own kernels; the cuBLAS GEMM of the tensor-core head is not counted). */

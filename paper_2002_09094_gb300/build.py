@@ -2,8 +2,8 @@
 
 Each translation unit under csrc/ is compiled in parallel, then linked into
 ``paper_2002_09094_gb300/libivfkm.so`` (CUDA runtime linked statically; at
-run time the library needs the CUDA driver and cuBLAS).  Nothing is installed
-into site-packages.
+run time the library needs only the CUDA driver).  Nothing is installed into
+site-packages.
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libivfkm.so")
-SOURCES = ["radix.cu", "assign.cu", "update.cu", "ivf_api.cu", "assign_static.cu"]
+SOURCES = ["radix.cu", "assign.cu", "update.cu", "ivf_api.cu", "assign_static.cu", "probe.cu", "tc_head.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
                 raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcublas"], capture_output=True, text=True)
+        r = subprocess.run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("nvcc link failed")

@@ -238,11 +238,14 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
     unsigned long long o = 0;
     if (lane == 0) o = atomicAdd(a.work, 1ull);
     o = __shfl_sync(IVF_FULL_MASK, o, 0);
-    if (o >= (unsigned long long)a.n_docs) break;
+    if (o >= (unsigned long long)(a.obj_list_n != nullptr ? (int64_t)*a.obj_list_n : a.n_docs)) break;
     const int64_t oi = (int64_t)o * a.obj_stride;
     int64_t i;
     int b;
-    if (a.obj_inst != nullptr) {
+    if (a.obj_list != nullptr) {
+      i = a.obj_list[oi];
+      b = a.n_inst > 1 ? find_instance(a.inst_docs, a.n_inst, i) : 0;
+    } else if (a.obj_inst != nullptr) {
       const int q = find_instance(a.obj_prefix, a.n_obj_inst, oi);
       b = a.obj_inst[q];
       i = a.inst_docs[b] + (oi - a.obj_prefix[q]);
@@ -256,8 +259,16 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
     const ErrBound bound = err_bound(m, a.nx[i], a.storage, nonneg, a.rho_head != nullptr);
     const int tile = a.tiled ? a.k_tile : K;
     const int n_tiles = a.tiled ? (K + a.k_tile - 1) / a.k_tile : 1;
+    if (a.tile_lo >= n_tiles) continue;  // tile-major: this object's tiles are all done
+    const int tile_end = min(n_tiles, a.tile_hi);
+    const bool finish = tile_end == n_tiles;
     float best = -INFINITY, second = -INFINITY;
     int bid = 0x7fffffff;
+    if (a.tile_lo > 0) {  // carry of the previous tile-major launch
+      best = a.best[i];
+      bid = a.assign[i];
+      second = a.gap[i];
+    }
     int ncand = 0;
     bool overflow = false;
     const unsigned long long entries_before = my_entries;
@@ -419,7 +430,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
     // one pass; with several (SPLIT), the sparse lists are scattered once per
     // tile and each sub-tile then walks the object's dense rows into registers.
     constexpr bool split = R > 0 && SPLIT;
-    for (int tt = 0; tt < n_tiles; ++tt) {
+    for (int tt = a.tile_lo; tt < tile_end; ++tt) {
       const int lo = tt * tile;
       const int cnt = min(tile, K - lo);
       // rho <- 0 over the tile
@@ -502,7 +513,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
       }
       warp_top2(tb, ti, ts);
       top2_merge(best, bid, second, tb, ti, ts);
-      if (a.rescore) {
+      if (a.rescore && a.preflag == nullptr) {
         const float thr = best - bound.e2(best);
         prune_candidates(cand_id, cand_val, ncand, thr, lane);
         if (ts >= thr) {
@@ -539,10 +550,31 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
       __syncwarp();
     }
 
+    if (!finish) {  // tile-major: carry (best, id, second) to the next launch
+      if (lane == 0) {
+        a.assign[i] = bid;
+        a.best[i] = best;
+        a.gap[i] = second;
+      }
+      __syncwarp();
+      continue;
+    }
     const float g = best - second;
     // An object that met no posting entry has rho = 0 exactly for every
-    // cluster: its lowest-id argmax is exact and needs no re-score.
-    const bool any_entry = __any_sync(IVF_FULL_MASK, my_entries != entries_before);
+    // cluster: its lowest-id argmax is exact and needs no re-score.  A
+    // tile-major launch saw only its own tiles' slices, so it asks the full
+    // list lengths instead.
+    bool any_entry;
+    if (a.tile_lo == 0) {
+      any_entry = __any_sync(IVF_FULL_MASK, my_entries != entries_before);
+    } else {
+      bool hit = false;
+      for (int64_t h = r0 + lane; h < r1 && !hit; h += 32) {
+        const int t = __ldg(a.term + h);
+        hit = __ldg(a.term_ptr + t + 1) > __ldg(a.term_ptr + t);
+      }
+      any_entry = __any_sync(IVF_FULL_MASK, hit);
+    }
     const float e2 = bound.e2(best);
     if (lane == 0) {
       a.assign[i] = bid;
@@ -551,7 +583,10 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
       if (a.err != nullptr) a.err[i] = any_entry ? 0.5f * e2 : 0.f;
       if (!any_entry) ++my_zero;
     }
-    if (a.rescore && any_entry && g <= e2) {
+    if (a.rescore && any_entry && g <= e2 && a.preflag != nullptr) {
+      // tile-major: the candidates are collected by an object-major pass
+      if (lane == 0) a.preflag[atomicAdd(a.n_preflag, 1u)] = (int32_t)i;
+    } else if (a.rescore && any_entry && g <= e2) {
       prune_candidates(cand_id, cand_val, ncand, best - e2, lane);
       unsigned slot = 0;
       if (lane == 0) slot = atomicAdd(a.n_flagged, 1u);

@@ -1,8 +1,7 @@
 // C ABI of libivfkm (include/ivf.h): context, device layout, autotuner,
 // CUDA-graph iterations.  All arithmetic of the method runs in the kernels of
-// assign.cu, update.cu and radix.cu, plus (FP16/BF16 storage only) the cuBLAS
-// GEMM of the tensor-core head; this file validates, allocates, copies and
-// launches.
+// assign.cu, update.cu, radix.cu and (FP16/BF16 tensor-core head) tc_head.cu;
+// this file validates, allocates, copies and launches.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -13,8 +12,6 @@
 #include <string>
 #include <tuple>
 #include <vector>
-
-#include <cublas_v2.h>
 
 #include "../../include/ivf.h"
 #include "common.cuh"
@@ -30,6 +27,9 @@ using namespace ivfk;
 
 namespace {
 
+// Tile-major assignments launch once per accumulator tile, up to this many.
+constexpr int kMaxTileLaunches = 128;
+
 // Counters the kernels update; one device block, mirrored into pinned host memory.
 struct DevCounters {
   unsigned long long work;
@@ -37,6 +37,10 @@ struct DevCounters {
   unsigned long long n_rescored;
   unsigned long long work_cls[4];   // work counters of the per-class launches (batched contexts)
   unsigned long long zero_sim;      // objects that met no posting entry in the last assignment
+  unsigned long long work_re;       // work counter of the object-major pass over near-ties
+  unsigned long long entries_re;    // entries of that pass (already counted by the sweep)
+  unsigned long long work_tile[kMaxTileLaunches];  // work counters of the tile-major launches
+  unsigned int n_preflag;           // near-ties found by a tile-major sweep
   unsigned int n_flagged;
   unsigned int status;
   double objective;
@@ -60,6 +64,11 @@ struct Shape {
   int head_sub = 1;   // dense-head sub-tiles (32 * head_r clusters) per shared-memory tile
   bool tc = false;    // head part by a tensor-core GEMM (16-bit storage, one instance)
   float head_theta = 0.f;  // a list covering at least this fraction of K is stored densely
+  // Tile-major schedule (tiled shapes): one launch per accumulator tile over
+  // all objects, so the rows and list slices of one tile are what the SMs
+  // share in L2 at a time; an object-major pass then collects the candidates
+  // of the near-ties.
+  bool tmajor = false;
 };
 
 // Dense head rows start with room for this much device memory and grow, when
@@ -147,6 +156,7 @@ struct ivf_ctx {
   float* best = nullptr;
   float* gap = nullptr;
   float* errb = nullptr;  // per object: bound on |best - rho_FP64|
+  int32_t* preflag = nullptr;  // near-ties of a tile-major sweep
   int32_t* flag_obj = nullptr;
   int32_t* flag_cnt = nullptr;
   int32_t* flag_cand = nullptr;
@@ -193,12 +203,13 @@ struct ivf_ctx {
   std::vector<ClassPlan> cls;
   bool use_classes = false;
   // tensor-core head: objects in batches of tc_batch; per batch the dense
-  // head values xh [tc_batch x head_max] and the GEMM result
-  // rho_h [tc_batch x kpad] (both 16-bit, the storage type)
-  cublasHandle_t blas = nullptr;
-  void* blas_ws = nullptr;
+  // head values xh [tc_batch x head_max] with their nonzero-chunk flags, and
+  // the product rho_h [tc_batch x kpad] (16-bit, the storage type); the dense
+  // rows transposed, wdT [kpad x head_max] (the K-major B operand)
   void* xh = nullptr;
   void* rho_h = nullptr;
+  void* wdT = nullptr;
+  uint8_t* chunk_nz = nullptr;
   int64_t tc_batch = 0;
   int64_t tc_alloc_rows = 0, tc_alloc_kpad = 0, tc_alloc_batch = 0;
   bool tuned = false;
@@ -348,6 +359,7 @@ ivf_status check_status(ivf_ctx* c) {
     if (st & STS_CAPACITY) return fail(c, IVF_E_OOM, "new means exceed the inverted-file capacity");
     if (st & STS_BAD_MEANS) return fail(c, IVF_E_INVALID, "a mean row has zero norm, bad or unsorted terms");
     if (st & STS_BAD_ROWS) return fail(c, IVF_E_INVALID, "object rows failed validation");
+    if (st & STS_TIMEOUT) return fail(c, IVF_E_TIMEOUT, "a bounded device wait ran out (tensor-core head)");
     return fail(c, IVF_E_INVALID, "device status error");
   }
   return IVF_OK;
@@ -444,6 +456,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->best, N);
   AL(c->gap, N);
   AL(c->errb, N);
+  AL(c->preflag, N);
   AL(c->flag_obj, N);
   AL(c->flag_cnt, N);
   c->cand_slots = std::min<int64_t>(N, int64_t(1) << 20);
@@ -587,6 +600,10 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
     a.d_heads = reinterpret_cast<int64_t*>(&c->dc->heads);
     a.zero_rows = c->shape.tc ? c->head_max : 0;  // the GEMM reads every row
     a.d_heads_wanted = reinterpret_cast<int64_t*>(&c->dc->heads_wanted);
+    if (c->shape.tc && c->wdT) {
+      a.wdT = c->wdT;
+      a.ldt = c->head_max;
+    }
   }
   return a;
 }
@@ -796,18 +813,25 @@ ivf_status ensure_toff(ivf_ctx* c, int k_tile) {
   return IVF_OK;
 }
 
-// Tensor-core head: a fixed number of dense rows (the GEMM depth), sized
-// from the lists that qualify now with a tenth of room, and the per-batch
-// buffers; lists beyond the rows are read sparsely (exact).
+// Tensor-core head: a fixed number of dense rows (the GEMM depth, a
+// multiple of the 64-slot K-chunk), sized from the lists that qualify now
+// with a tenth of room, their transposed copy, and the per-batch buffers;
+// lists beyond the rows are read sparsely (exact).
 ivf_status setup_tc(ivf_ctx* c, long long wanted) {
   const int64_t vb = (int64_t)storage_bytes(c->cfg.storage);
-  const int64_t rows = std::min<int64_t>(c->Dt, std::max<int64_t>(64, ((wanted + wanted / 10) + 63) / 64 * 64));
-  if (rows != c->head_max) {
+  const int64_t rows =
+      std::min<int64_t>(ceil_div(c->Dt, 64) * 64, std::max<int64_t>(64, ((wanted + wanted / 10) + 63) / 64 * 64));
+  if (rows != c->head_max || !c->wdT) {
     dfree(c, c->wd);
+    dfree(c, c->wdT);
     c->wd = nullptr;
+    c->wdT = nullptr;
     char* p = nullptr;
     ST(dalloc(c, &p, rows * c->kpad * vb));
     c->wd = p;
+    char* q = nullptr;
+    ST(dalloc(c, &q, rows * c->kpad * vb));
+    c->wdT = q;
     c->head_max = rows;
   }
   // batches: GEMM output of at most ~3 GB, a multiple of 128 objects
@@ -816,40 +840,36 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
   if (!c->xh || c->tc_alloc_rows != rows || c->tc_alloc_batch != c->tc_batch || c->tc_alloc_kpad != c->kpad) {
     dfree(c, c->xh);
     dfree(c, c->rho_h);
+    dfree(c, c->chunk_nz);
     c->xh = nullptr;
     c->rho_h = nullptr;
+    c->chunk_nz = nullptr;
     char* x = nullptr;
     ST(dalloc(c, &x, c->tc_batch * rows * 2));
     c->xh = x;
     char* r = nullptr;
     ST(dalloc(c, &r, c->tc_batch * c->kpad * 2));
     c->rho_h = r;
+    ST(dalloc(c, &c->chunk_nz, ceil_div(c->tc_batch, 128) * (rows / 64)));
     c->tc_alloc_rows = rows;
     c->tc_alloc_batch = c->tc_batch;
     c->tc_alloc_kpad = c->kpad;
   }
-  if (!c->blas) {
-    if (cublasCreate(&c->blas) != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasCreate failed");
-    char* ws = nullptr;
-    const int64_t ws_bytes = int64_t(32) << 20;
-    ST(dalloc(c, &ws, ws_bytes));
-    c->blas_ws = ws;
-    // a fixed workspace: no allocation inside the GEMM, so it can be captured in a graph
-    if (cublasSetWorkspace(c->blas, c->blas_ws, (size_t)ws_bytes) != CUBLAS_STATUS_SUCCESS)
-      return fail(c, IVF_E_CUDA, "cublasSetWorkspace failed");
-  }
-  if (cublasSetStream(c->blas, c->stream) != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasSetStream failed");
   return IVF_OK;
 }
 
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
-  if (!sh.tc && c->xh) {  // the tensor-core batch buffers are only kept while in use
+  if (!sh.tc && (c->xh || c->wdT)) {  // the tensor-core buffers are only kept while in use
     CK(c, cudaStreamSynchronize(c->stream));
     dfree(c, c->xh);
     dfree(c, c->rho_h);
+    dfree(c, c->chunk_nz);
+    dfree(c, c->wdT);
     c->xh = nullptr;
     c->rho_h = nullptr;
+    c->chunk_nz = nullptr;
+    c->wdT = nullptr;
     c->tc_alloc_rows = c->tc_alloc_batch = c->tc_alloc_kpad = 0;
   }
   c->shape = sh;
@@ -874,19 +894,27 @@ ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
 }
 
 // One batch of the tensor-core head: dense head values of objects
-// [b0, b0 + nb), then rho_h = xh . wd (cuBLAS, FP32 accumulation, output in
-// the storage type): rho_h is nb x kpad row-major, i.e. the column-major
-// kpad x nb product of wd^T (kpad x head_max, leading dimension kpad) and
-// xh^T (head_max x nb).
+// [b0, b0 + nb) with their nonzero-chunk flags, then
+// rho_h[i][c] = sum_s xh[i][s] * wdT[c][s] on the tensor cores (tc_head.cu:
+// FP32 accumulation in TMEM, output in the storage type).
 ivf_status enqueue_tc_gemm(ivf_ctx* c, int64_t b0, int64_t nb) {
-  CK(c, launch_build_xhead(b0, nb, c->row_ptr, c->term, c->val_store, c->head_slot, c->xh, c->head_max, c->stream));
-  const cudaDataType dt = c->cfg.storage == IVF_BF16 ? CUDA_R_16BF : CUDA_R_16F;
-  const float one = 1.f, zero = 0.f;
-  const cublasStatus_t st =
-      cublasGemmEx(c->blas, CUBLAS_OP_N, CUBLAS_OP_N, (int)c->kpad, (int)nb, (int)c->head_max, &one, c->wd, dt,
-                   (int)c->kpad, c->xh, dt, (int)c->head_max, &zero, c->rho_h, dt, (int)c->kpad,
-                   CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-  if (st != CUBLAS_STATUS_SUCCESS) return fail(c, IVF_E_CUDA, "cublasGemmEx failed");
+  CK(c, launch_build_xhead(b0, nb, c->row_ptr, c->term, c->val_store, c->head_slot, c->xh, c->head_max,
+                           c->chunk_nz, c->stream));
+  TcHeadArgs h;
+  h.m = nb;
+  h.n = (int32_t)c->kpad;
+  h.k = (int32_t)c->head_max;
+  h.a = c->xh;
+  h.lda = c->head_max;
+  h.b = c->wdT;
+  h.ldb = c->head_max;
+  h.d = c->rho_h;
+  h.ldd = c->kpad;
+  h.bf16 = c->cfg.storage == IVF_BF16;
+  h.chunk_nz = c->chunk_nz;
+  h.status = &c->dc->status;
+  h.num_sms = c->num_sms;
+  CK(c, launch_tc_head(h, c->stream));
   return IVF_OK;
 }
 
@@ -902,6 +930,45 @@ ivf_status enqueue_tc_batch(ivf_ctx* c, const Shape& sh, int target, int rescore
   a.obj_stride = (int32_t)obj_stride;
   a.n_docs = (nb + obj_stride - 1) / obj_stride;
   CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
+  return IVF_OK;
+}
+
+// The assignment launches of shape sh over a (the main path: every object,
+// or a strided sample of them).  Tile-major shapes launch once per tile with
+// the (best, id, second) carry in best / assign / gap, then, when a.rescore,
+// run the object-major kernel over the near-ties the sweep found, which
+// collects their candidate clusters (same arithmetic, so the same bits) and
+// queues them for the FP64 re-score.
+ivf_status enqueue_main_launches(ivf_ctx* c, const Shape& sh, AssignArgs a) {
+  if (!sh.tmajor) {
+    CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
+    return IVF_OK;
+  }
+  const int n_tiles = (int)ceil_div(c->kmax, sh.k_tile);
+  if (n_tiles > kMaxTileLaunches) return fail(c, IVF_E_UNSUPPORTED, "too many tiles for a tile-major sweep");
+  CK(c, cudaMemsetAsync(c->dc->work_tile, 0, sizeof(unsigned long long) * n_tiles, c->stream));
+  CK(c, cudaMemsetAsync(&c->dc->n_preflag, 0, sizeof(unsigned int), c->stream));
+  const int rescore = a.rescore;
+  for (int t = 0; t < n_tiles; ++t) {
+    AssignArgs at = a;
+    at.tile_lo = t;
+    at.tile_hi = t + 1;
+    at.work = &c->dc->work_tile[t];
+    at.preflag = c->preflag;
+    at.n_preflag = &c->dc->n_preflag;
+    CK(c, launch_assign(at, sh.warps, sh.blocks, c->stream, sh.head_r));
+  }
+  if (rescore) {
+    AssignArgs ar = a;
+    ar.obj_list = c->preflag;
+    ar.obj_list_n = &c->dc->n_preflag;
+    ar.obj_stride = 1;
+    ar.work = &c->dc->work_re;
+    ar.entries = &c->dc->entries_re;
+    ar.n_zero_sim = nullptr;
+    CK(c, cudaMemsetAsync(&c->dc->work_re, 0, sizeof(unsigned long long), c->stream));
+    CK(c, launch_assign(ar, sh.warps, sh.blocks, c->stream, sh.head_r));
+  }
   return IVF_OK;
 }
 
@@ -948,7 +1015,10 @@ ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
   for (int rep = 0; rep < 2; ++rep) {
     CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), c->stream));
     CK(c, cudaEventRecord(c->ev[0], c->stream));
-    CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
+    if (q < 0)
+      ST(enqueue_main_launches(c, sh, a));
+    else
+      CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
     CK(c, cudaEventRecord(c->ev[1], c->stream));
     CK(c, cudaEventSynchronize(c->ev[1]));
     float ms = 0.f;
@@ -1068,10 +1138,32 @@ ivf_status autotune(ivf_ctx* c) {
         }
     }
   }
+  // Tile-major twins of the tiled shapes (single-instance contexts, CUDA-core
+  // head or sparse kernel): IVF_FLAG_TILE_MAJOR keeps only those,
+  // IVF_FLAG_OBJECT_MAJOR none of them.
+  {
+    const bool only_t = (c->cfg.flags & IVF_FLAG_TILE_MAJOR) != 0;
+    const bool no_t = (c->cfg.flags & IVF_FLAG_OBJECT_MAJOR) != 0;
+    std::vector<Shape> with_t;
+    for (const Shape& s0 : cands) {
+      const bool can = s0.tiled && !s0.tc && !c->use_classes && ceil_div(c->kmax, s0.k_tile) <= kMaxTileLaunches;
+      if (!only_t || !can) {
+        if (!only_t) with_t.push_back(s0);
+      }
+      if (can && !no_t) {
+        Shape s1 = s0;
+        s1.tmajor = true;
+        with_t.push_back(s1);
+      }
+    }
+    if (only_t && with_t.empty()) return fail(c, IVF_E_UNSUPPORTED, "no tiled shape for a tile-major sweep");
+    cands.swap(with_t);
+  }
   if (cands.empty()) return fail(c, IVF_E_UNSUPPORTED, "no accumulator tile fits shared memory");
   // Contexts of the same shape in one process reuse the first choice, so
   // their FP32 rounding (which depends on the kernel family) is the same.
-  const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY | IVF_FLAG_TENSOR_HEAD));
+  const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY | IVF_FLAG_TENSOR_HEAD |
+                                           IVF_FLAG_TILE_MAJOR | IVF_FLAG_OBJECT_MAJOR));
   auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
                              (c->cfg.storage * 32 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
                              c->n_inst);
@@ -1149,8 +1241,7 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
     for (int64_t b0 = 0; b0 < c->N; b0 += c->tc_batch)
       ST(enqueue_tc_batch(c, c->shape, target, c->cfg.rescore, b0, std::min<int64_t>(c->tc_batch, c->N - b0), 1));
   } else {
-    AssignArgs a = assign_args(c, c->shape, target, c->cfg.rescore);
-    CK(c, launch_assign(a, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
+    ST(enqueue_main_launches(c, c->shape, assign_args(c, c->shape, target, c->cfg.rescore)));
   }
   if (timed) CK(c, timing_event(c, &e1));
   if (c->cfg.rescore) {
@@ -1337,6 +1428,7 @@ ivf_status redo_update_if_overflow(ivf_ctx* c, int src, long long* heads_wanted 
       CK(c, cudaMemcpyAsync(heads_wanted, &c->dc->heads_wanted, sizeof(long long), cudaMemcpyDeviceToHost,
                             c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (st & STS_TIMEOUT) return check_status(c);
     if (!(st & STS_CAPACITY)) return IVF_OK;
     CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), c->stream));
     ST(grow_means(c, e_new + e_new / 4 + 4096));
@@ -1406,7 +1498,6 @@ void ivf_destroy(ivf_ctx* ctx) {
   for (auto& ev : ctx->ev)
     if (ev) cudaEventDestroy(ev);
   for (auto& ev : ctx->tev) cudaEventDestroy(ev);
-  if (ctx->blas) cublasDestroy(ctx->blas);
   for (void* p : ctx->allocs) cudaFree(p);
   if (ctx->hc) cudaFreeHost(ctx->hc);
   delete ctx;
@@ -1585,6 +1676,7 @@ ivf_status ivf_assign(ivf_ctx* c, int32_t* assign_out, float* best_out, float* g
   if (gap_out) CK(c, cudaMemcpyAsync(gap_out, c->gap, sizeof(float) * c->N, cudaMemcpyDeviceToDevice, c->stream));
   if (stats_out) {
     ST(read_counters(c));
+    if (c->hc->status & STS_TIMEOUT) return check_status(c);
     fill_stats(c, stats_out);
     CK(c, cudaEventElapsedTime(&stats_out->t_assign_ms, c->ev[0], c->ev[1]));
   }
@@ -1736,6 +1828,7 @@ ivf_status ivf_get_info(ivf_ctx* c, ivf_info* out) {
     CK(c, cudaMemcpy(&heads, &c->dc->heads, sizeof(long long), cudaMemcpyDeviceToHost));
   }
   out->dense_head_rows = heads;
+  out->tile_major = c->shape.tmajor ? 1 : 0;
   return IVF_OK;
 }
 

@@ -18,6 +18,7 @@ enum StatusBits : unsigned {
   STS_CAPACITY = 1u,   // the new means did not fit the inverted-file capacity
   STS_BAD_MEANS = 2u,  // a mean row given by the caller has zero norm or bad terms
   STS_BAD_ROWS = 4u,   // object rows failed validation
+  STS_TIMEOUT = 8u,    // a bounded device wait ran out
 };
 
 // Everything the assignment kernel reads and writes.
@@ -79,6 +80,22 @@ struct AssignArgs {
   const void* rho_head;
   int64_t rho_ld;
   int64_t obj_base;
+  // Tile-major schedule: this launch covers the accumulator tiles
+  // [tile_lo, tile_hi) of every object (tile_hi = INT_MAX: to the last).  An
+  // object whose tiles end inside the range is finished here (gap, error
+  // bound, zero-similarity count, near-tie test); otherwise (best, id,
+  // second) are carried to the next launch in best / assign / gap.  With
+  // tile_lo > 0 the carry of the previous launch is read first.  A finished
+  // near-tie is not re-scored here: it is appended to preflag (count in
+  // *n_preflag) for an object-major pass that collects its candidates.
+  int32_t tile_lo = 0;
+  int32_t tile_hi = 0x7fffffff;
+  int32_t* preflag = nullptr;
+  unsigned int* n_preflag = nullptr;
+  // Object-major pass over a list of objects (the near-ties of a tile-major
+  // sweep): work item o is object obj_list[o], o < *obj_list_n.
+  const int32_t* obj_list = nullptr;
+  const unsigned int* obj_list_n = nullptr;
 };
 
 // Registers per lane of the head accumulator; the tile is 32 * R clusters.
@@ -219,6 +236,8 @@ struct IvfBuildArgs {
   int64_t* d_heads;      // [1] receives the number of dense rows
   int64_t zero_rows;     // rows of wd cleared before filling (0: the rows in use)
   int64_t* d_heads_wanted;  // [1] receives the number of lists that qualified (may exceed head_max)
+  void* wdT = nullptr;       // tensor-core head: transposed rows [kpad x ldt] (K-major B operand), or null
+  int64_t ldt = 0;
   // scratch
   uint32_t* k32a;
   uint32_t* k32b;
@@ -251,10 +270,37 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
                                    unsigned* status, unsigned* negative, cudaStream_t s);
 
 // Dense 16-bit head values of objects [i0, i0 + nb): x[(i - i0) * ldx + head_slot[t]] = val[h]
-// for every head term t of object i, zeros elsewhere.
+// for every head term t of object i, zeros elsewhere; chunk_nz (or null)
+// [ceil(nb / 128) x ldx / 64] gets 1 for every (128-object block, 64-slot
+// chunk) holding a value.
 cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
                                const void* val16, const int32_t* head_slot, void* x, int64_t ldx,
-                               cudaStream_t s);
+                               uint8_t* chunk_nz, cudaStream_t s);
+
+// Tensor-core head product (tc_head.cu): d[i][c] = sum_s a[i][s] * b[c][s]
+// for i < m, c < n, s < k; a, b, d 16-bit (bf16 or fp16), row-major with
+// leading dimensions lda, ldb, ldd (elements, multiples of 8; pointers
+// 16-byte aligned), FP32 accumulation, d rounded to the 16-bit type.
+// n a multiple of 256, k a multiple of 64.  chunk_nz (or null): per
+// 128-row block of a and 64-column chunk, 0 when that chunk of a is zero
+// (skipped).  A bounded wait that runs out sets STS_TIMEOUT in *status.
+struct TcHeadArgs {
+  int64_t m;
+  int32_t n, k;
+  const void* a;
+  int64_t lda;
+  const void* b;
+  int64_t ldb;
+  void* d;
+  int64_t ldd;
+  bool bf16;
+  const uint8_t* chunk_nz;
+  unsigned* status;
+  int num_sms;
+};
+cudaError_t launch_tc_head(const TcHeadArgs& h, cudaStream_t s);
+// Transpose the dense head rows wd [rows x kpad] into wdT [kpad x ldt] (16-bit).
+cudaError_t launch_transpose16(const void* wd, int64_t rows, int64_t kpad, void* wdT, int64_t ldt, cudaStream_t s);
 cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s);
 
 }  // namespace ivfk

@@ -580,6 +580,7 @@ cudaError_t launch_build_head(const IvfBuildArgs& a, cudaStream_t s) {
       break;
   }
   IVF_LAUNCH_CHECK();
+  if (a.wdT != nullptr) IVF_CU(launch_transpose16(a.wd, a.head_max, a.kpad, a.wdT, a.ldt, s));
   return cudaSuccess;
 }
 
@@ -649,28 +650,60 @@ cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsi
   return cudaSuccess;
 }
 
-// Warp per object: scatter its head-term values into its dense row.
+// Warp per object: scatter its head-term values into its dense row, and
+// flag the (128-object block, 64-slot chunk) pairs that hold a value (every
+// writer stores the same 1).
 __global__ void k_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
-                              const uint16_t* val16, const int32_t* head_slot, uint16_t* x, int64_t ldx) {
+                              const uint16_t* val16, const int32_t* head_slot, uint16_t* x, int64_t ldx,
+                              uint8_t* chunk_nz) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t nchunks = ldx / 64;
   for (int64_t o = gw; o < nb; o += nw) {
     const int64_t i = i0 + o;
     for (int64_t h = row_ptr[i] + lane; h < row_ptr[i + 1]; h += 32) {
       const int32_t s = head_slot[term[h]];
-      if (s >= 0) x[o * ldx + s] = val16[h];
+      if (s >= 0) {
+        x[o * ldx + s] = val16[h];
+        if (chunk_nz != nullptr) chunk_nz[(o >> 7) * nchunks + (s >> 6)] = 1;
+      }
     }
   }
 }
 
 cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, const int32_t* term,
                                const void* val16, const int32_t* head_slot, void* x, int64_t ldx,
-                               cudaStream_t s) {
+                               uint8_t* chunk_nz, cudaStream_t s) {
   IVF_CU(cudaMemsetAsync(x, 0, sizeof(uint16_t) * nb * ldx, s));
+  if (chunk_nz != nullptr) IVF_CU(cudaMemsetAsync(chunk_nz, 0, (size_t)((nb + 127) / 128) * (ldx / 64), s));
   k_build_xhead<<<grid_for(nb * 32, T256, 16384), T256, 0, s>>>(i0, nb, row_ptr, term,
                                                                  static_cast<const uint16_t*>(val16), head_slot,
-                                                                 static_cast<uint16_t*>(x), ldx);
+                                                                 static_cast<uint16_t*>(x), ldx, chunk_nz);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// 32 x 32 tiles through shared memory: wdT[c][r] = wd[r][c].
+__global__ void k_transpose16(const uint16_t* __restrict__ wd, int64_t rows, int64_t kpad, uint16_t* __restrict__ wdT,
+                              int64_t ldt) {
+  __shared__ uint16_t tile[32][33];
+  const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t r = r0 + y, c = c0 + threadIdx.x;
+    tile[y][threadIdx.x] = (r < rows && c < kpad) ? wd[r * kpad + c] : (uint16_t)0;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+    const int64_t c = c0 + y, r = r0 + threadIdx.x;
+    if (c < kpad && r < ldt) wdT[c * ldt + r] = tile[threadIdx.x][y];
+  }
+}
+
+cudaError_t launch_transpose16(const void* wd, int64_t rows, int64_t kpad, void* wdT, int64_t ldt, cudaStream_t s) {
+  const dim3 grid((unsigned)((kpad + 31) / 32), (unsigned)((ldt + 31) / 32));
+  k_transpose16<<<grid, dim3(32, 8), 0, s>>>(static_cast<const uint16_t*>(wd), rows, kpad,
+                                             static_cast<uint16_t*>(wdT), ldt);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }

@@ -28,6 +28,9 @@ IVF_FLAG_NO_GRAPH = 2
 IVF_FLAG_DENSE_HEAD = 4
 IVF_FLAG_SPARSE_ONLY = 8
 IVF_FLAG_TENSOR_HEAD = 16
+IVF_FLAG_TILE_MAJOR = 32
+IVF_FLAG_OBJECT_MAJOR = 64
+SCHEDULE_FLAGS = {"auto": 0, "tile_major": IVF_FLAG_TILE_MAJOR, "object_major": IVF_FLAG_OBJECT_MAJOR}
 KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG_SPARSE_ONLY,
                 "tensor_head": IVF_FLAG_TENSOR_HEAD}
 
@@ -36,7 +39,7 @@ EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_fro
            "ivf_update", "ivf_iterate", "ivf_get_assign", "ivf_get_best", "ivf_get_gap", "ivf_get_info",
            "ivf_get_err_bound", "ivf_get_means", "ivf_get_inverted_file", "ivf_get_members", "ivf_set_assign", "ivf_restore_means",
            "ivf_last_error", "ivf_destroy", "ivf_launch_count", "ivf_version", "ivfb_create", "ivfb_get_changed",
-           "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static"]
+           "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static", "ivf_probe_l2_read", "ivf_head_product"]
 IVF_STATIC_MAX_DOCS = 16384
 IVF_STATIC_MAX_K = 12288
 
@@ -83,7 +86,7 @@ class Info(ctypes.Structure):
                 ("dense_head_r", ctypes.c_int32), ("dense_head_sub", ctypes.c_int32),
                 ("dense_head_tensor", ctypes.c_int32),
                 ("dense_head_theta", ctypes.c_float),
-                ("dense_head_rows", ctypes.c_int64)]
+                ("dense_head_rows", ctypes.c_int64), ("tile_major", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -129,6 +132,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ivf_timing_reset": ([vp, i32], st),
         "ivf_get_timing": ([vp, P(Timing)], st),
         "ivf_assign_static": ([i64, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
+        "ivf_probe_l2_read": ([i64, i32, vp, ctypes.POINTER(ctypes.c_double)], st),
+        "ivf_head_product": ([i64, i32, i32, vp, i64, vp, i64, vp, i64, i32, vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +145,30 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
 
 def launch_count() -> int:
     return int(load_library().ivf_launch_count())
+
+
+def head_product(a, b, d, storage: str, stream=None) -> None:
+    """d = a @ b.T on the tensor cores (ivf_head_product); a (m x k), b (n x k),
+    d (m x n): 16-bit CUDA tensors (torch) with unit column stride."""
+    for t in (a, b, d):
+        if not t.is_cuda or t.stride(1) != 1:
+            raise ValueError("head_product takes row-major CUDA tensors")
+    s = _default_stream() if stream is None else stream
+    st = load_library().ivf_head_product(int(a.shape[0]), int(b.shape[0]), int(a.shape[1]), a.data_ptr(), a.stride(0),
+                                         b.data_ptr(), b.stride(0), d.data_ptr(), d.stride(0), STORAGE[storage],
+                                         ctypes.c_void_p(s))
+    if st != 0:
+        raise IvfError(st, "ivf_head_product failed")
+
+
+def probe_l2_read_gbs(nbytes: int = 48 << 20, reps: int = 64, stream=None) -> float:
+    """Read bandwidth (GB/s) of a resident set served by L2 (ivf_probe_l2_read)."""
+    out = ctypes.c_double(0.0)
+    s = _default_stream() if stream is None else stream
+    st = load_library().ivf_probe_l2_read(int(nbytes), int(reps), ctypes.c_void_p(s), ctypes.byref(out))
+    if st != 0:
+        raise IvfError(st, "ivf_probe_l2_read failed")
+    return float(out.value)
 
 
 def _ptr(x: Any, dtype) -> tuple[int, Any]:
@@ -181,6 +210,8 @@ class IVF:
     are re-scored in FP64 when ``rescore``); ``kernel`` restricts the
     autotuner to one family -- "auto", "sparse", "dense_head" (CUDA-core dense
     rows) or "tensor_head" (FP16/BF16: dense rows as a tensor-core GEMM);
+    ``schedule`` restricts it to "tile_major" (one launch per cluster tile
+    over all objects) or "object_major" shapes (default "auto": either);
     ``k_tile`` / ``warps_per_block`` fix the launch shape instead of tuning
     it; ``means_capacity`` and ``dense_head_bytes`` size the first
     allocations (both grow on demand); ``use_graph`` lets ``iterate`` replay
@@ -191,7 +222,7 @@ class IVF:
     def __init__(self, row_ptr, term, val, n_terms: int, k: int, storage: str = "f32", rescore: bool = True,
                  empty_policy: int = 0, k_tile: int = 0, warps_per_block: int = 0, validate: bool = False,
                  use_graph: bool = True, stream=None, kernel: str = "auto", means_capacity: int = 0,
-                 dense_head_bytes: int = 0, _batched=None):
+                 dense_head_bytes: int = 0, schedule: str = "auto", _batched=None):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p(0)
         self._loading = None
@@ -200,7 +231,8 @@ class IVF:
         vptr, vk = _ptr(val, np.float32)
         n_docs = int(len(row_ptr) - 1)
         nnz = int(len(term))
-        flags = (IVF_FLAG_VALIDATE if validate else 0) | (0 if use_graph else IVF_FLAG_NO_GRAPH) | KERNEL_FLAGS[kernel]
+        flags = ((IVF_FLAG_VALIDATE if validate else 0) | (0 if use_graph else IVF_FLAG_NO_GRAPH) |
+                 KERNEL_FLAGS[kernel] | SCHEDULE_FLAGS[schedule])
         cfg = Config(n_docs=n_docs, n_terms=int(n_terms), nnz=nnz, k=int(k), storage=STORAGE[storage],
                      rescore=1 if rescore else 0, empty_policy=int(empty_policy), k_tile=int(k_tile),
                      warps_per_block=int(warps_per_block), flags=flags, means_capacity=int(means_capacity),

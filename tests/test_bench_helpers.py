@@ -24,6 +24,17 @@ def test_traffic_only_for_the_unchanged_kernel_and_the_same_workload(tmp_path, m
     assert bench.traffic_per_launch("wl-a", "f32") is None
 
 
+def test_traffic_of_the_schedule_in_use_and_l2_bytes(tmp_path, monkeypatch):
+    sha = hashlib.sha256(open(bench.ASSIGN_SRC, "rb").read()).hexdigest()
+    p = tmp_path / "traffic.txt"
+    p.write_text(f"assign_cu_sha256: {sha}\nworkload: wl\nschedule[f32]: tile_major\n"
+                 "bytes_per_launch[f32]: 1000\nl2_bytes_per_launch[f32]: 5000\n")
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(p))
+    assert bench.traffic_per_launch("wl", "f32", "tile_major") == 1000.0
+    assert bench.traffic_per_launch("wl", "f32", "tile_major", what="l2_bytes") == 5000.0
+    assert bench.traffic_per_launch("wl", "f32", "object_major") is None   # taken under another schedule
+
+
 def test_committed_traffic_file_parses():
     """The committed summary names a workload and an FP32 byte count; whether
     it applies is decided at run time by the kernel source's hash."""

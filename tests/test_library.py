@@ -21,7 +21,7 @@ def lib():
 def declared_functions():
     text = open(os.path.join(ROOT, "include", "ivf.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ivfb?_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(ivfb?_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
