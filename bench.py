@@ -33,7 +33,8 @@ import numpy as np  # noqa: E402
 METRIC = "sec/Lloyd iteration & assign-step HBM GB/s (% peak); mixed vs FP32 at equal assigns"
 UNIT = "s/iter"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "assign_kernel_dram_traffic.txt")
-ASSIGN_SRC = os.path.join(ROOT, "paper_2002_09094_gb300", "csrc", "assign.cu")
+# the assignment kernel's sources: counters taken on another version do not apply
+ASSIGN_SRCS = [os.path.join(ROOT, "paper_2002_09094_gb300", "csrc", f) for f in ("assign.cu", "assign_common.cuh")]
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -48,8 +49,9 @@ def parse():
     p.add_argument("--n-docs", type=int, default=0, help="use only this many documents of the workload "
                    "(same generator; for small profiling cases)")
     p.add_argument("--k", type=int, default=0, help="override the number of clusters (profiling cases)")
-    p.add_argument("--kernel", choices=["auto", "dense_head", "sparse", "tensor_head"], default="auto",
-                   help="assignment kernel family (auto = the autotuner picks)")
+    p.add_argument("--kernel", choices=["auto", "dense_head", "sparse", "tensor_head", "ivfd"], default="auto",
+                   help="assignment kernel family (auto = the autotuner picks; ivfd = the comparison "
+                        "algorithm IVFD, Algorithm 4)")
     p.add_argument("--instances", type=int, default=256, help="instances of --workload batched")
     p.add_argument("--e2e-steps", type=int, default=0,
                    help="steps of the end-to-end leg (0 = as many as --steps)")
@@ -87,6 +89,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def assign_sources_sha() -> str:
+    """sha256 over the assignment kernel's source files, in order."""
+    h = hashlib.sha256()
+    for p in ASSIGN_SRCS:
+        h.update(open(p, "rb").read())
+    return h.hexdigest()
+
+
 def traffic_per_launch(workload_name: str, storage: str, schedule: str | None = None, what: str = "bytes"):
     """DRAM bytes (what="bytes") or L2 bytes (what="l2_bytes") per assignment
     step from the committed ncu summary, or None when the kernel source
@@ -97,8 +107,8 @@ def traffic_per_launch(workload_name: str, storage: str, schedule: str | None = 
         text = open(TRAFFIC_FILE).read()
     except OSError:
         return None
-    sha = hashlib.sha256(open(ASSIGN_SRC, "rb").read()).hexdigest()
-    m_sha = re.search(r"assign_cu_sha256:\s*([0-9a-f]+)", text)
+    sha = assign_sources_sha()
+    m_sha = re.search(r"assign_src_sha256:\s*([0-9a-f]+)", text)
     if not m_sha or m_sha.group(1) != sha:
         return None
     m_w = re.search(r"^workload:\s*(\S+)", text, re.M)

@@ -80,6 +80,15 @@ typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
                                     device memory between launches (tiled shapes, one instance) */
 #define IVF_FLAG_OBJECT_MAJOR 64u /* autotune only among object-major schedules (each object walks all
                                      of its cluster tiles in one launch) */
+#define IVF_FLAG_IVFD 128u  /* the paper's comparison algorithm IVFD (Algorithm 4, Section 7.2) instead
+                               of IVF for the assignment step: the objects are also held as an
+                               inverted file (term-major (object, value) lists, built once per object
+                               set) and the assignment loops over the means, each mean's terms
+                               scattering into per-object accumulators.  Same multiplications
+                               (Eq. 15) and, for FP32, the same similarity bits as IVF's sparse
+                               kernel; near-ties are re-scored in FP64 against every cluster.  FP32
+                               storage, one instance (else IVF_E_UNSUPPORTED).  The update step is
+                               IVF's (the paper's IVFD also updates from the standard sparse form). */
 
 typedef struct {
   int64_t n_docs;      /* N >= 1 */
@@ -95,7 +104,9 @@ typedef struct {
                           else a power of two in [512, 65536] or >= k (no tiling);
                           with IVF_FLAG_DENSE_HEAD it fixes the dense-head kernel's
                           shared-memory tile (512: 512-cluster head tile; 1024 and
-                          more: k_tile / 1024 head tiles of 1,024 clusters) */
+                          more: k_tile / 1024 head tiles of 1,024 clusters), with
+                          IVF_FLAG_TENSOR_HEAD the same for the tensor-core head
+                          (a multiple of 1024; theta 0.25) */
   int32_t warps_per_block; /* 0 = autotune, else 1..32 */
   uint32_t flags;      /* IVF_FLAG_* */
   int32_t means_capacity; /* entries reserved for the means / inverted file at create
@@ -196,6 +207,38 @@ ivf_status ivf_assign(ivf_ctx* ctx, int32_t* assign_out, float* best_out, float*
  * check that the new means fit; if not, it grows the arrays and redoes the
  * step (IVF_E_OOM if the device has no room). */
 ivf_status ivf_update(ivf_ctx* ctx);
+
+/* Data-parallel update over object shards (one context per rank, each
+ * holding a contiguous shard of the objects and the same means).  The
+ * update of Algorithm 3 sums each cluster's members; split by shard,
+ *   s_j = sum over shards r of s_j^(r),  s_j^(r) = sum_{i in C_j, i in shard r} x_i,
+ * so each rank computes its own member sums, the ranks exchange them, and
+ * every rank finishes the same update from all of them.
+ *
+ * ivf_get_partial_sums: this context's member sums for its last assignment
+ * (the first half of the update step), before normalisation.  *n_out (host)
+ * receives U, the number of (cluster, term) pairs its members touch; when
+ * any of cluster / term / sum is given (host or device, capacity cap >= U,
+ * else IVF_E_INVALID), they receive cluster int32[U] (cluster ids), term
+ * int32[U] and sum double[U] (FP64, members in ascending object id), in
+ * ascending (cluster, term).  A sum can be exactly 0 (values of both signs).
+ * One-instance contexts only.  Synchronises the stream. */
+ivf_status ivf_get_partial_sums(ivf_ctx* ctx, int64_t cap, int32_t* cluster, int32_t* term, double* sum,
+                                int64_t* n_out);
+/* ivf_update_from_partials: the update step from member sums gathered from
+ * every shard -- the shards' lists as ivf_get_partial_sums returns them,
+ * concatenated in shard order (n_total entries; host or device arrays,
+ * copied in).  Equal (cluster, term) pairs are added in FP64 in the order
+ * given (shard order), so every rank that passes the same lists gets the
+ * same bits; then, as ivf_update: normalisation, the empty-cluster policy
+ * (from this context's current means), and the inverted-file rebuild.  An
+ * id outside [0, k) or [0, n_terms) is IVF_E_INVALID before any change.
+ * Synchronises the stream.  The sums of one shard alone give ivf_update's
+ * means exactly; with several shards, each sum is the shards' partial sums
+ * added in shard order (FP64 reassociated against the one-context order,
+ * about 1e-16 relative). */
+ivf_status ivf_update_from_partials(ivf_ctx* ctx, int64_t n_total, const int32_t* cluster, const int32_t* term,
+                                    const double* sum);
 
 /* Run assignment + update until no assignment changes (from the second
  * iteration on) or max_iter iterations.  Synchronises once per iteration to
@@ -322,7 +365,10 @@ ivf_status ivfb_get_changed(ivf_ctx* ctx, int64_t* out);
  *
  * The caller passes every input and output as DEVICE pointers:
  *   objects: row_ptr int64[N+1], term int32[nnz], val float[nnz] (CSR, as
- *     for ivf_create);
+ *     for ivf_create).  They are read only and NOT validated: row_ptr must
+ *     start at 0 and not decrease, terms must be ascending, unique and in
+ *     [0, n_terms) in each row, and values finite; rows that break this give
+ *     undefined results (a term id out of range is read out of bounds);
  *   the inverted file of the means: term_ptr int64[D+1], cid int32[E]
  *     (cluster ids, ascending inside each term's list), w float[E];
  *   the FP64 means it was cast from, cluster-major: mean_ptr int64[K+1],
@@ -346,7 +392,8 @@ ivf_status ivfb_get_changed(ivf_ctx* ctx, int64_t* out);
  * capture.  All calls share the one array, which keeps the last call's
  * contents (each call clears what must start at zero): calls that overlap
  * on the GPU -- from two streams or two threads -- race, so the caller must
- * serialise them. */
+ * serialise them.  The call returns after enqueueing its kernels on
+ * cuda_stream. */
 #define IVF_STATIC_MAX_DOCS 16384
 #define IVF_STATIC_MAX_K 12288
 #define IVF_STATIC_SCRATCH_BYTES 2425088

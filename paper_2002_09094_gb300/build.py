@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libivfkm.so")
-SOURCES = ["radix.cu", "assign.cu", "update.cu", "ivf_api.cu", "assign_static.cu", "probe.cu", "tc_head.cu"]
+SOURCES = ["radix.cu", "assign.cu", "update.cu", "ivf_api.cu", "assign_static.cu", "probe.cu", "tc_head.cu",
+           "ivfd.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

@@ -141,7 +141,8 @@ extern "C" ivf_status ivf_assign_static(int64_t n_docs, const int64_t* row_ptr, 
   if (cudaGetLastError() != cudaSuccess) return IVF_E_CUDA;
   // the sign flag is not read here: the call uses the bound valid for signed values
   unsigned* negative = reinterpret_cast<unsigned*>(scratch + kTables + 128);
-  if (launch_prepare_objects(n_docs, 0, 0, row_ptr, const_cast<int32_t*>(term), val, nullptr, ST_F32, nx, 1,
+  // the caller's rows are read only (no term rebase: one instance, offset 0)
+  if (launch_prepare_objects(n_docs, 0, 0, row_ptr, term, nullptr, val, nullptr, ST_F32, nx, 1,
                              tab->docs, tab->toff, tab->terms, 0, &ctr->status, negative, s) != cudaSuccess)
     return IVF_E_CUDA;
 

@@ -27,8 +27,10 @@ using namespace ivfk;
 
 namespace {
 
-// Tile-major assignments launch once per accumulator tile, up to this many.
+// Tile-major assignments launch once per accumulator tile, up to this many,
+// and carry up to kTileCand re-score candidates per object between launches.
 constexpr int kMaxTileLaunches = 128;
+constexpr int kTileCand = 32;
 
 // Counters the kernels update; one device block, mirrored into pinned host memory.
 struct DevCounters {
@@ -157,6 +159,33 @@ struct ivf_ctx {
   float* gap = nullptr;
   float* errb = nullptr;  // per object: bound on |best - rho_FP64|
   int32_t* preflag = nullptr;  // near-ties of a tile-major sweep
+  int64_t run_cap = 0;         // entries of flags / starts (+1) and ukey / usum
+  // member sums gathered from shards (ivf_update_from_partials)
+  int32_t* part_cluster = nullptr;
+  int32_t* part_term = nullptr;
+  double* part_sum = nullptr;
+  int64_t part_cap = 0, part_n = 0;
+  int64_t* d_part_n = nullptr;
+  // candidate carry of tile-major sweeps: [N x kTileCand] ids and values, [N] counts
+  int32_t* tcand = nullptr;
+  float* tcandv = nullptr;
+  int32_t* tcand_n = nullptr;
+  // zeta: the objects' tuples in term-major order (term, and object << 32 |
+  // value bits, ascending object inside each term), rebuilt with the objects;
+  // the update step sorts it by cluster, IVFD reads it as the objects'
+  // inverted file
+  int64_t* zptr = nullptr;
+  uint32_t* zterm = nullptr;
+  uint64_t* zov = nullptr;
+  // IVFD (IVF_FLAG_IVFD): per-(term, sub-range) offsets into zeta, built once
+  // per object set, and the per-(mean chunk, object) top-2
+  bool ivfd_built = false;
+  int32_t* zoff = nullptr;
+  int64_t z_sub = 0;
+  int32_t z_chunks = 0;
+  float* z_pbest = nullptr;
+  float* z_psecond = nullptr;
+  int32_t* z_pid = nullptr;
   int32_t* flag_obj = nullptr;
   int32_t* flag_cnt = nullptr;
   int32_t* flag_cand = nullptr;
@@ -214,6 +243,8 @@ struct ivf_ctx {
   int64_t tc_alloc_rows = 0, tc_alloc_kpad = 0, tc_alloc_batch = 0;
   bool tuned = false;
   bool tuned_on_updated_means = false;  // the choice was made on means from an update step
+  int64_t e_tuned = 0;   // inverted-file entries when the choice was made
+  int32_t tunings = 0;   // choices made so far (bounded)
   // state
   bool means_set = false;
   int64_t cand_slots = 0;      // flagged objects with room for a candidate list
@@ -367,6 +398,8 @@ ivf_status check_status(ivf_ctx* c) {
 
 // --------------------------------------------------------------- create
 
+ivf_status enqueue_build_zeta(ivf_ctx* c);
+
 ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vector<int64_t>& inst_docs,
                          const std::vector<int32_t>& inst_terms, const std::vector<int32_t>& inst_k,
                          const int64_t* row_ptr, const int32_t* term, const float* val, void* stream,
@@ -500,11 +533,16 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->starts, nnz + 1);
   AL(c->ukey, nnz);
   AL(c->usum, nnz);
+  c->run_cap = nnz;
+  AL(c->d_part_n, 1);
   AL(c->uptr, c->Kt + 1);
   AL(c->newlen, c->Kt + 1);
   AL(c->d_nnz, 1);
   AL(c->d_n, 1);
   AL(c->d_u, 1);
+  AL(c->zptr, c->Dt + 1);
+  AL(c->zterm, std::max<int64_t>(1, nnz));
+  AL(c->zov, std::max<int64_t>(1, nnz));
 #undef AL
   e = cudaMallocHost(&c->hc, sizeof(DevCounters));
   if (e != cudaSuccess) return bail(fail_cuda(c, "cudaMallocHost", e));
@@ -537,12 +575,13 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   const int64_t dn[2] = {nnz, N};
   CKB(cudaMemcpyAsync(c->d_nnz, &dn[0], sizeof(int64_t), cudaMemcpyHostToDevice, st));
   CKB(cudaMemcpyAsync(c->d_n, &dn[1], sizeof(int64_t), cudaMemcpyHostToDevice, st));
-  CKB(launch_prepare_objects(N, nnz, 0, c->row_ptr, c->term, c->val32,
+  CKB(launch_prepare_objects(N, nnz, 0, c->row_ptr, c->term, c->term, c->val32,
                              cfg->storage == IVF_F32 ? nullptr : c->val_store, cfg->storage, c->nx, n_inst,
                              c->inst_docs, c->inst_toff, c->inst_terms, (cfg->flags & IVF_FLAG_VALIDATE) ? 1 : 0,
                              &c->dc->status, &c->dc->negative, st));
 #undef CKB
   if ((s = check_status(c)) != IVF_OK) return bail(s);
+  if ((s = enqueue_build_zeta(c)) != IVF_OK) return bail(s);
   *out = c;
   return IVF_OK;
 }
@@ -556,6 +595,7 @@ ivf_status validate_cfg(const ivf_config* cfg) {
   if (cfg->means_capacity < 0) return IVF_E_INVALID;
   if (cfg->dense_head_bytes < 0) return IVF_E_INVALID;
   if (cfg->k_tile < 0) return IVF_E_INVALID;
+  if ((cfg->flags & IVF_FLAG_IVFD) && cfg->storage != IVF_F32) return IVF_E_UNSUPPORTED;
   return IVF_OK;
 }
 
@@ -685,6 +725,46 @@ bool device_resident(const void* p) {
 // device) and prepares it as at create time.  Called by the calls that start
 // from the objects (assignment, iterate, initial means from documents); the
 // update step keeps working on the objects its assignment ran on.
+IvfdArgs ivfd_args(ivf_ctx* c, int target, int rescore) {
+  IvfdArgs a{};
+  a.n_docs = c->N;
+  a.nnz = c->nnz;
+  a.dt = c->Dt;
+  a.k = (int32_t)c->Kt;
+  a.row_ptr = c->row_ptr;
+  a.term = c->term;
+  a.val32 = c->val32;
+  a.nx = c->nx;
+  a.zptr = c->zptr;
+  a.zov = c->zov;
+  a.zoff = c->zoff;
+  a.n_sub = c->z_sub;
+  a.mptr = c->mptr[c->mcur];
+  a.mterm = c->mterm[c->mcur];
+  a.mval = c->mval[c->mcur];
+  a.term_ptr = c->term_ptr;
+  a.chunks = c->z_chunks;
+  a.pbest = c->z_pbest;
+  a.psecond = c->z_psecond;
+  a.pid = c->z_pid;
+  a.assign = c->assign[target];
+  a.best = c->best;
+  a.gap = c->gap;
+  a.err = c->errb;
+  a.entries = &c->dc->entries;
+  a.n_zero_sim = &c->dc->zero_sim;
+  a.rescore = rescore;
+  a.n_flagged = &c->dc->n_flagged;
+  a.flag_obj = c->flag_obj;
+  a.flag_cnt = c->flag_cnt;
+  a.preflag = c->preflag;
+  a.n_preflag = &c->dc->n_preflag;
+  a.nonneg = 1;
+  a.negative = &c->dc->negative;
+  a.means_negative = &c->dc->means_negative[c->mcur];
+  return a;
+}
+
 ivf_status commit_objects(ivf_ctx* c) {
   if (!c->objects_pending) return IVF_OK;
   c->objects_pending = false;
@@ -695,12 +775,53 @@ ivf_status commit_objects(ivf_ctx* c) {
   CK(c, cudaMemcpyAsync(c->val32, c->st_val32, sizeof(float) * c->nnz, cudaMemcpyDeviceToDevice, s));
   CK(c, cudaEventRecord(c->ev_staging_free, s));
   CK(c, cudaMemsetAsync(&c->dc->negative, 0, sizeof(unsigned), s));
-  CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->val32,
+  CK(c, launch_prepare_objects(c->N, c->nnz, 0, c->row_ptr, c->term, c->term, c->val32,
                                c->cfg.storage == IVF_F32 ? nullptr : c->val_store, c->cfg.storage, c->nx, c->n_inst,
                                c->inst_docs, c->inst_toff, c->inst_terms, (c->cfg.flags & IVF_FLAG_VALIDATE) ? 1 : 0,
                                &c->dc->status, &c->dc->negative, s));
   if (c->cfg.flags & IVF_FLAG_VALIDATE) ST(check_status(c));
+  ST(enqueue_build_zeta(c));
   c->members_valid = false;
+  c->ivfd_built = false;
+  return IVF_OK;
+}
+
+// IVFD: zeta and its offsets for the current objects (allocates on first use;
+// called before any stream capture).
+ivf_status ensure_ivfd(ivf_ctx* c) {
+  if (c->ivfd_built) return IVF_OK;
+  if (!c->zoff) {
+    c->z_sub = ivfd_sub_ranges(c->N);
+    c->z_chunks = (int32_t)std::max<int64_t>(1, std::min<int64_t>(c->Kt, ceil_div(64 * (int64_t)c->num_sms, c->z_sub)));
+    ST(dalloc(c, &c->zoff, c->Dt * (c->z_sub + 1)));
+    ST(dalloc(c, &c->z_pbest, c->z_chunks * c->N));
+    ST(dalloc(c, &c->z_psecond, c->z_chunks * c->N));
+    ST(dalloc(c, &c->z_pid, c->z_chunks * c->N));
+  }
+  IvfdArgs a = ivfd_args(c, 0, 0);
+  CK(c, launch_build_ivfd_offsets(a, c->stream));
+  c->ivfd_built = true;
+  return IVF_OK;
+}
+
+// zeta of the current objects (stream-ordered; after every object load).
+ivf_status enqueue_build_zeta(ivf_ctx* c) {
+  ZetaArgs z{};
+  z.n_docs = c->N;
+  z.nnz = c->nnz;
+  z.dt = c->Dt;
+  z.row_ptr = c->row_ptr;
+  z.term = c->term;
+  z.val32 = c->val32;
+  z.zptr = c->zptr;
+  z.zterm = c->zterm;
+  z.zov = c->zov;
+  z.k32 = c->v32a;
+  z.v64 = c->k64a;
+  z.temp = c->temp;
+  z.d_nnz = c->d_nnz;
+  z.tbits = c->tbits;
+  CK(c, launch_build_zeta(z, c->stream));
   return IVF_OK;
 }
 
@@ -860,6 +981,11 @@ ivf_status setup_tc(ivf_ctx* c, long long wanted) {
 
 ivf_status set_shape(ivf_ctx* c, const Shape& sh) {
   if (sh.tiled) ST(ensure_toff(c, sh.k_tile));
+  if (sh.tmajor && !c->tcand) {  // kept once allocated (the autotuner switches shapes)
+    ST(dalloc(c, &c->tcand, c->N * (int64_t)kTileCand));
+    ST(dalloc(c, &c->tcandv, c->N * (int64_t)kTileCand));
+    ST(dalloc(c, &c->tcand_n, c->N));
+  }
   if (!sh.tc && (c->xh || c->wdT)) {  // the tensor-core buffers are only kept while in use
     CK(c, cudaStreamSynchronize(c->stream));
     dfree(c, c->xh);
@@ -918,6 +1044,8 @@ ivf_status enqueue_tc_gemm(ivf_ctx* c, int64_t b0, int64_t nb) {
   return IVF_OK;
 }
 
+ivf_status enqueue_main_launches(ivf_ctx* c, const Shape& sh, AssignArgs a);
+
 // Assignment of objects [b0, b0 + nb) with the tensor-core head part.
 ivf_status enqueue_tc_batch(ivf_ctx* c, const Shape& sh, int target, int rescore, int64_t b0, int64_t nb,
                             int64_t obj_stride) {
@@ -929,7 +1057,7 @@ ivf_status enqueue_tc_batch(ivf_ctx* c, const Shape& sh, int target, int rescore
   a.obj_base = b0;
   a.obj_stride = (int32_t)obj_stride;
   a.n_docs = (nb + obj_stride - 1) / obj_stride;
-  CK(c, launch_assign(a, sh.warps, sh.blocks, c->stream, sh.head_r));
+  ST(enqueue_main_launches(c, sh, a));
   return IVF_OK;
 }
 
@@ -956,6 +1084,12 @@ ivf_status enqueue_main_launches(ivf_ctx* c, const Shape& sh, AssignArgs a) {
     at.work = &c->dc->work_tile[t];
     at.preflag = c->preflag;
     at.n_preflag = &c->dc->n_preflag;
+    if (rescore && c->tcand) {
+      at.tcand = c->tcand;
+      at.tcandv = c->tcandv;
+      at.tcand_n = c->tcand_n;
+      at.tcand_cap = kTileCand;
+    }
     CK(c, launch_assign(at, sh.warps, sh.blocks, c->stream, sh.head_r));
   }
   if (rescore) {
@@ -995,7 +1129,7 @@ ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
     for (int rep = 0; rep < 2; ++rep) {
       CK(c, cudaMemsetAsync(c->dc, 0, offsetof(DevCounters, status), c->stream));
       CK(c, cudaEventRecord(c->ev[0], c->stream));
-      ST(enqueue_tc_batch(c, sh, target, 0, 0, nb, 1));
+      ST(enqueue_tc_batch(c, sh, target, c->cfg.rescore, 0, nb, 1));
       CK(c, cudaEventRecord(c->ev[1], c->stream));
       CK(c, cudaEventSynchronize(c->ev[1]));
       float ms = 0.f;
@@ -1005,7 +1139,9 @@ ivf_status time_shape(ivf_ctx* c, const Shape& sh, int q, float* ms_out) {
     *ms_out = ms_min / (float)nb;
     return IVF_OK;
   }
-  AssignArgs a = assign_args(c, sh, target, 0);
+  // with the re-score on, the candidate bookkeeping (and a tile-major
+  // sweep's pass over the near-ties) is part of what is timed
+  AssignArgs a = assign_args(c, sh, target, c->cfg.rescore);
   set_class_objs(c, a, q);
   const int64_t n = a.n_docs;
   const int64_t stride = std::max<int64_t>(1, std::min<int64_t>(16, n >> 16));
@@ -1070,14 +1206,30 @@ ivf_status tune_classes(ivf_ctx* c) {
 // posting lists); the lists of updated means are far denser, which favours
 // other kernels, so the choice is made once more on the first assignment
 // after an update step.
-bool needs_tuning(const ivf_ctx* c) { return !c->tuned || (!c->tuned_on_updated_means && c->iteration > 0); }
+// The means keep densifying over the first iterations, so the choice is
+// also remade (up to four choices in all) whenever the inverted file has
+// grown by more than a third since the last one.
+// (IVFD: its object inverted file is rebuilt here after the objects change.)
+bool needs_tuning(const ivf_ctx* c) {
+  return !c->tuned || (!c->tuned_on_updated_means && c->iteration > 0) ||
+         (c->iteration > 0 && c->tunings < 4 && 3 * c->e_cur > 4 * c->e_tuned) ||
+         ((c->cfg.flags & IVF_FLAG_IVFD) && !c->ivfd_built);
+}
 
 ivf_status autotune(ivf_ctx* c) {
+  // IVFD: the object inverted file, and (below) a sparse object-major IVF
+  // shape for the pass that collects the near-ties' candidates
+  const bool ivfd = (c->cfg.flags & IVF_FLAG_IVFD) != 0;
+  if (ivfd) ST(ensure_ivfd(c));
   std::vector<Shape> cands;
   Shape sh;
   if (c->cfg.k_tile > 0) {
     bool ok;
-    if (c->cfg.flags & IVF_FLAG_DENSE_HEAD) {
+    if (c->cfg.flags & IVF_FLAG_TENSOR_HEAD) {
+      ok = c->cfg.storage != IVF_F32 && c->n_inst == 1 && c->cfg.k_tile % (32 * HEAD_R_LARGE) == 0 &&
+           shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh, HEAD_R_LARGE, 0.25f,
+                     c->cfg.k_tile / (32 * HEAD_R_LARGE), true);
+    } else if (c->cfg.flags & IVF_FLAG_DENSE_HEAD) {
       const int hr = c->cfg.k_tile < 32 * HEAD_R_LARGE ? HEAD_R_MID : HEAD_R_LARGE;
       ok = c->cfg.k_tile % (32 * hr) == 0 &&
            shape_for(c, c->kmax, 0, c->cfg.warps_per_block, &sh, hr, 0.25f, c->cfg.k_tile / (32 * hr));
@@ -1089,7 +1241,7 @@ ivf_status autotune(ivf_ctx* c) {
   } else {
     const bool tc_only = (c->cfg.flags & IVF_FLAG_TENSOR_HEAD) != 0;
     const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0 || tc_only;
-    const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0;
+    const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0 || ivfd;
     // tensor-core head: 16-bit storage, one instance, K over one 1,024-cluster tile
     const bool tc_ok = !no_head && c->cfg.storage != IVF_F32 && c->n_inst == 1 && c->kmax > 32 * HEAD_R_LARGE;
     if (tc_ok && (tc_only || !(c->cfg.flags & IVF_FLAG_DENSE_HEAD)))  // DENSE_HEAD: the CUDA-core head
@@ -1138,15 +1290,15 @@ ivf_status autotune(ivf_ctx* c) {
         }
     }
   }
-  // Tile-major twins of the tiled shapes (single-instance contexts, CUDA-core
-  // head or sparse kernel): IVF_FLAG_TILE_MAJOR keeps only those,
-  // IVF_FLAG_OBJECT_MAJOR none of them.
+  // Tile-major twins of the tiled shapes (single-instance contexts; with the
+  // tensor-core head, tile-major within each batch of objects):
+  // IVF_FLAG_TILE_MAJOR keeps only those, IVF_FLAG_OBJECT_MAJOR none of them.
   {
-    const bool only_t = (c->cfg.flags & IVF_FLAG_TILE_MAJOR) != 0;
-    const bool no_t = (c->cfg.flags & IVF_FLAG_OBJECT_MAJOR) != 0;
+    const bool only_t = (c->cfg.flags & IVF_FLAG_TILE_MAJOR) != 0 && !ivfd;
+    const bool no_t = (c->cfg.flags & IVF_FLAG_OBJECT_MAJOR) != 0 || ivfd;
     std::vector<Shape> with_t;
     for (const Shape& s0 : cands) {
-      const bool can = s0.tiled && !s0.tc && !c->use_classes && ceil_div(c->kmax, s0.k_tile) <= kMaxTileLaunches;
+      const bool can = s0.tiled && !c->use_classes && ceil_div(c->kmax, s0.k_tile) <= kMaxTileLaunches;
       if (!only_t || !can) {
         if (!only_t) with_t.push_back(s0);
       }
@@ -1165,7 +1317,7 @@ ivf_status autotune(ivf_ctx* c) {
   const int kflags = (int)(c->cfg.flags & (IVF_FLAG_DENSE_HEAD | IVF_FLAG_SPARSE_ONLY | IVF_FLAG_TENSOR_HEAD |
                                            IVF_FLAG_TILE_MAJOR | IVF_FLAG_OBJECT_MAJOR));
   auto key = std::make_tuple(c->N >> 12, (int64_t)c->kmax, c->Dt >> 12,
-                             (c->cfg.storage * 32 + kflags) * 2 + (c->iteration > 0 ? 1 : 0),
+                             (c->cfg.storage * 256 + kflags) * 8 + std::min(c->tunings, 7),
                              c->n_inst);
   const bool cacheable = c->cfg.k_tile == 0 && c->cfg.warps_per_block == 0;
   {
@@ -1177,6 +1329,8 @@ ivf_status autotune(ivf_ctx* c) {
       if (!c->cls.empty()) c->cls.back().shape = c->shape;
       c->tuned = true;
       c->tuned_on_updated_means = c->iteration > 0;
+      c->e_tuned = c->e_cur;
+      ++c->tunings;
       return IVF_OK;
     }
   }
@@ -1199,6 +1353,8 @@ ivf_status autotune(ivf_ctx* c) {
   if (c->use_classes) ST(tune_classes(c));
   c->tuned = true;
   c->tuned_on_updated_means = c->iteration > 0;
+  c->e_tuned = c->e_cur;
+  ++c->tunings;
   if (cacheable) {
     TuneChoice tc;
     tc.main = best_sh;
@@ -1229,7 +1385,20 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
   CK(c, cudaMemsetAsync(c->inst_changed, 0, sizeof(long long) * c->n_inst, s));
   size_t e0 = 0, e1 = 0, e2 = 0;
   if (timed) CK(c, timing_event(c, &e0));
-  if (c->use_classes) {
+  if (c->cfg.flags & IVF_FLAG_IVFD) {
+    CK(c, cudaMemsetAsync(&c->dc->n_preflag, 0, sizeof(unsigned int), s));
+    CK(c, launch_assign_ivfd(ivfd_args(c, target, c->cfg.rescore), s));
+    if (c->cfg.rescore) {  // the near-ties' candidates, from the IVF kernel (same sums)
+      AssignArgs ar = assign_args(c, c->shape, target, 1);
+      ar.obj_list = c->preflag;
+      ar.obj_list_n = &c->dc->n_preflag;
+      ar.work = &c->dc->work_re;
+      ar.entries = &c->dc->entries_re;
+      ar.n_zero_sim = nullptr;
+      CK(c, cudaMemsetAsync(&c->dc->work_re, 0, sizeof(unsigned long long), s));
+      CK(c, launch_assign(ar, c->shape.warps, c->shape.blocks, s, c->shape.head_r));
+    }
+  } else if (c->use_classes) {
     // one launch per class of instances, each with the kernel chosen for it
     for (size_t q = 0; q < c->cls.size(); ++q) {
       const Shape& sh = c->cls[q].shape;
@@ -1294,8 +1463,9 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
   return IVF_OK;
 }
 
-// Update from assignment buffer `src`: means mcur -> mcur^1, then the inverted file.
-ivf_status enqueue_update(ivf_ctx* c, int src) {
+// Everything the update kernels read and write, from assignment buffer src:
+// means mcur -> mcur^1.
+UpdateArgs update_args(ivf_ctx* c, int src) {
   const int mo = c->mcur, mn = c->mcur ^ 1;
   UpdateArgs u{};
   u.n_docs = c->N;
@@ -1312,6 +1482,8 @@ ivf_status enqueue_update(ivf_ctx* c, int src) {
   u.inst_docs = c->inst_docs;
   u.inst_clu = c->inst_clu;
   u.assign = c->assign[src];
+  u.zterm = c->zterm;
+  u.zov = c->zov;
   u.empty_policy = c->cfg.empty_policy;
   u.mptr_old = c->mptr[mo];
   u.mterm_old = c->mterm[mo];
@@ -1340,9 +1512,51 @@ ivf_status enqueue_update(ivf_ctx* c, int src) {
   u.temp = c->temp;
   u.status = &c->dc->status;
   u.means_negative = &c->dc->means_negative[mn];
+  return u;
+}
+
+// Update from assignment buffer `src`: means mcur -> mcur^1, then the inverted file.
+ivf_status enqueue_update(ivf_ctx* c, int src) {
+  UpdateArgs u = update_args(c, src);
   CK(c, cudaMemsetAsync(u.means_negative, 0, sizeof(unsigned), c->stream));
   CK(c, launch_update_means(u, c->stream));
-  ST(enqueue_build_ivf(c, mn));
+  ST(enqueue_build_ivf(c, c->mcur ^ 1));
+  return IVF_OK;
+}
+
+// Run buffers (flags, starts, ukey, usum) and sort scratch for n run sums.
+ivf_status ensure_runs(ivf_ctx* c, int64_t n) {
+  if (n > c->run_cap) {
+    void* olds[] = {c->flags, c->starts, c->ukey, c->usum};
+    for (void* p : olds) dfree(c, p);
+    c->flags = nullptr;
+    c->starts = nullptr;
+    c->ukey = nullptr;
+    c->usum = nullptr;
+    ST(dalloc(c, &c->flags, n + 1));
+    ST(dalloc(c, &c->starts, n + 1));
+    ST(dalloc(c, &c->ukey, n));
+    ST(dalloc(c, &c->usum, n));
+    c->run_cap = n;
+    drop_graphs(c);
+  }
+  if (n > c->scratch_len) ST(alloc_scratch(c, n));
+  return IVF_OK;
+}
+
+// Update from the member sums in part_* (gathered from shards): means
+// mcur -> mcur^1, then the inverted file.
+ivf_status enqueue_update_from_partials(ivf_ctx* c) {
+  UpdateArgs u = update_args(c, c->alatest >= 0 ? c->alatest : 0);
+  PartialArgs p{};
+  p.n_max = std::max<int64_t>(1, c->part_n);
+  p.d_n = c->d_part_n;
+  p.cluster = c->part_cluster;
+  p.term = c->part_term;
+  p.sum = c->part_sum;
+  CK(c, cudaMemsetAsync(u.means_negative, 0, sizeof(unsigned), c->stream));
+  CK(c, launch_update_from_partials(u, p, c->stream));
+  ST(enqueue_build_ivf(c, c->mcur ^ 1));
   return IVF_OK;
 }
 
@@ -1418,7 +1632,8 @@ ivf_status grow_means(ivf_ctx* c, int64_t new_cap) {
 // Synchronises.
 // heads_wanted (optional) receives the number of lists that qualified as
 // dense rows in the rebuilt inverted file, read in the same synchronisation.
-ivf_status redo_update_if_overflow(ivf_ctx* c, int src, long long* heads_wanted = nullptr) {
+ivf_status redo_update_if_overflow(ivf_ctx* c, int src, long long* heads_wanted = nullptr,
+                                   bool from_partials = false) {
   for (int attempt = 0; attempt < 4; ++attempt) {
     unsigned st = 0;
     int64_t e_new = 0;
@@ -1429,10 +1644,16 @@ ivf_status redo_update_if_overflow(ivf_ctx* c, int src, long long* heads_wanted 
                             c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     if (st & STS_TIMEOUT) return check_status(c);
-    if (!(st & STS_CAPACITY)) return IVF_OK;
+    if (!(st & STS_CAPACITY)) {
+      c->e_cur = e_new;
+      return IVF_OK;
+    }
     CK(c, cudaMemsetAsync(&c->dc->status, 0, sizeof(unsigned), c->stream));
     ST(grow_means(c, e_new + e_new / 4 + 4096));
-    ST(enqueue_update(c, src));
+    if (from_partials)
+      ST(enqueue_update_from_partials(c));
+    else
+      ST(enqueue_update(c, src));
   }
   return fail(c, IVF_E_OOM, "new means exceed the inverted-file capacity after growing it");
 }
@@ -1459,6 +1680,8 @@ ivf_status finish_set_means(ivf_ctx* c) {
   // fresh one given the same data
   c->tuned = false;
   c->tuned_on_updated_means = false;
+  c->tunings = 0;
+  c->e_tuned = 0;
   c->members_valid = false;
   drop_graphs(c);
   return IVF_OK;
@@ -1525,6 +1748,7 @@ ivf_status ivfb_create(const ivf_config* cfg, int32_t n_inst, const int64_t* ins
   *out = nullptr;
   if (validate_cfg(cfg) != IVF_OK || n_inst < 1 || !inst_docs || !inst_terms || !inst_k || !row_ptr)
     return IVF_E_INVALID;
+  if (cfg->flags & IVF_FLAG_IVFD) return IVF_E_UNSUPPORTED;
   std::vector<int64_t> docs(n_inst + 1);
   std::vector<int32_t> terms(n_inst), ks(n_inst);
   if (cudaMemcpy(docs.data(), inst_docs, sizeof(int64_t) * (n_inst + 1), cudaMemcpyDefault) != cudaSuccess ||
@@ -1703,6 +1927,80 @@ ivf_status ivf_update(ivf_ctx* c) {
   return IVF_OK;
 }
 
+ivf_status ivf_get_partial_sums(ivf_ctx* c, int64_t cap, int32_t* cluster, int32_t* term, double* sum,
+                                int64_t* n_out) {
+  if (!c || !n_out) return fail(c, IVF_E_INVALID, "null argument");
+  if (c->n_inst != 1) return fail(c, IVF_E_UNSUPPORTED, "partial sums of a batched context");
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  if (c->alatest < 0) return fail(c, IVF_E_STATE, "no assignment to sum from");
+  UpdateArgs u = update_args(c, c->alatest);
+  CK(c, launch_member_sums(u, c->stream));
+  int64_t n = 0;
+  CK(c, cudaMemcpyAsync(&n, c->d_u, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  *n_out = n;
+  if (!cluster && !term && !sum) return IVF_OK;
+  if (cap < n) return fail(c, IVF_E_INVALID, "output capacity below the number of member sums");
+  if (n > c->part_cap) {
+    dfree(c, c->part_cluster);
+    dfree(c, c->part_term);
+    dfree(c, c->part_sum);
+    c->part_cluster = nullptr;
+    c->part_term = nullptr;
+    c->part_sum = nullptr;
+    ST(dalloc(c, &c->part_cluster, n));
+    ST(dalloc(c, &c->part_term, n));
+    ST(dalloc(c, &c->part_sum, n));
+    c->part_cap = n;
+  }
+  CK(c, launch_partial_out(u, std::max<int64_t>(1, n), c->part_cluster, c->part_term, c->part_sum, c->stream));
+  if (cluster) CK(c, cudaMemcpyAsync(cluster, c->part_cluster, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream));
+  if (term) CK(c, cudaMemcpyAsync(term, c->part_term, sizeof(int32_t) * n, cudaMemcpyDefault, c->stream));
+  if (sum) CK(c, cudaMemcpyAsync(sum, c->part_sum, sizeof(double) * n, cudaMemcpyDefault, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return IVF_OK;
+}
+
+ivf_status ivf_update_from_partials(ivf_ctx* c, int64_t n_total, const int32_t* cluster, const int32_t* term,
+                                    const double* sum) {
+  if (!c || n_total < 0 || (n_total > 0 && (!cluster || !term || !sum))) return fail(c, IVF_E_INVALID, "bad arguments");
+  if (c->n_inst != 1) return fail(c, IVF_E_UNSUPPORTED, "partial sums of a batched context");
+  if (!c->means_set) return fail(c, IVF_E_STATE, "means not set");
+  if (n_total >= (int64_t(1) << 32) - 2) return fail(c, IVF_E_UNSUPPORTED, "too many member sums");
+  ST(ensure_runs(c, std::max<int64_t>(1, n_total)));
+  if (n_total > c->part_cap) {
+    dfree(c, c->part_cluster);
+    dfree(c, c->part_term);
+    dfree(c, c->part_sum);
+    c->part_cluster = nullptr;
+    c->part_term = nullptr;
+    c->part_sum = nullptr;
+    ST(dalloc(c, &c->part_cluster, n_total));
+    ST(dalloc(c, &c->part_term, n_total));
+    ST(dalloc(c, &c->part_sum, n_total));
+    c->part_cap = n_total;
+  }
+  if (n_total > 0) {
+    CK(c, cudaMemcpyAsync(c->part_cluster, cluster, sizeof(int32_t) * n_total, cudaMemcpyDefault, c->stream));
+    CK(c, cudaMemcpyAsync(c->part_term, term, sizeof(int32_t) * n_total, cudaMemcpyDefault, c->stream));
+    CK(c, cudaMemcpyAsync(c->part_sum, sum, sizeof(double) * n_total, cudaMemcpyDefault, c->stream));
+  }
+  // the ids are checked on the device copy before they key a sort
+  c->part_n = n_total;
+  CK(c, cudaMemcpyAsync(c->d_part_n, &c->part_n, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  CK(c, launch_check_partials(n_total, c->part_cluster, c->part_term, (int32_t)c->Kt, (int32_t)c->Dt,
+                              &c->dc->status, c->stream));
+  ST(check_status(c));
+  ST(enqueue_update_from_partials(c));
+  long long wanted = 0;
+  ST(redo_update_if_overflow(c, c->alatest, &wanted, true));
+  c->mcur ^= 1;
+  c->iteration += 1;
+  c->members_valid = false;
+  ST(grow_head_if_needed(c, wanted));
+  return IVF_OK;
+}
+
 ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_t* converged,
                        ivf_iter_stats* last_stats) {
   if (!c) return IVF_E_INVALID;
@@ -1754,6 +2052,7 @@ ivf_status ivf_iterate(ivf_ctx* c, int32_t max_iter, int32_t* iters_done, int32_
     c->mcur ^= 1;
     c->iteration += 1;
     c->members_valid = true;
+    c->e_cur = c->hc->ivf_e;
     ++done;
     ST(grow_head_if_needed(c, c->hc->heads_wanted));
     if (c->hc->status) ST(check_status(c));

@@ -92,6 +92,14 @@ struct AssignArgs {
   int32_t tile_hi = 0x7fffffff;
   int32_t* preflag = nullptr;
   unsigned int* n_preflag = nullptr;
+  // Tile-major candidate carry: each object's candidate clusters for the
+  // FP64 re-score collected so far (ids and FP32 values, at most tcand_cap;
+  // count -1 = more), so a near-tie needs no second pass unless its list
+  // overflowed.  Null = not kept (every near-tie goes to preflag).
+  int32_t* tcand = nullptr;   // [N x tcand_cap]
+  float* tcandv = nullptr;    // [N x tcand_cap]
+  int32_t* tcand_n = nullptr; // [N]
+  int32_t tcand_cap = 0;
   // Object-major pass over a list of objects (the near-ties of a tile-major
   // sweep): work item o is object obj_list[o], o < *obj_list_n.
   const int32_t* obj_list = nullptr;
@@ -173,6 +181,10 @@ struct UpdateArgs {
   const int32_t* inst_clu;
   const int64_t* inst_toff;  // [n_inst+1] first global term id of each instance
   const int32_t* assign;  // local cluster ids
+  // the objects' tuples in term-major order (zeta): term, and (object << 32
+  // | FP32 value bits) of each, ascending object inside each term
+  const uint32_t* zterm;
+  const uint64_t* zov;
   int32_t empty_policy;
   // old and new cluster-major means
   const int64_t* mptr_old;
@@ -205,7 +217,31 @@ struct UpdateArgs {
   unsigned* status;
   unsigned* means_negative;  // set when a written mean value is negative (zeroed by the caller)
 };
+// The whole update step: members, member sums, new means.
 cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s);
+// Members and member sums (ukey, usum, *d_u) only.
+cudaError_t launch_member_sums(const UpdateArgs& a, cudaStream_t s);
+// The new means from the run sums (ukey, usum, *d_u <= u_max); a.flags and
+// a.starts must hold u_max + 1 entries, ukey / usum u_max.
+cudaError_t launch_means_from_sums(const UpdateArgs& a, int64_t u_max, cudaStream_t s);
+// Member sums out of (ukey, usum, *d_u): local cluster, term, FP64 sum.
+cudaError_t launch_partial_out(const UpdateArgs& a, int64_t u_max, int32_t* cluster, int32_t* term, double* sum,
+                               cudaStream_t s);
+// Member sums gathered from shards (one instance): (cluster, term, sum)
+// lists concatenated in shard order, *d_n <= n_max entries (device).
+// Equal (cluster, term) are added in FP64 in the order given, then the new
+// means follow as in launch_means_from_sums (u_max = n_max).
+struct PartialArgs {
+  int64_t n_max;
+  const int64_t* d_n;
+  const int32_t* cluster;
+  const int32_t* term;
+  const double* sum;
+};
+cudaError_t launch_update_from_partials(const UpdateArgs& a, const PartialArgs& p, cudaStream_t s);
+// Every cluster id in [0, k) and term id in [0, d); a violation sets STS_BAD_ROWS.
+cudaError_t launch_check_partials(int64_t n, const int32_t* cluster, const int32_t* term, int32_t k, int32_t d,
+                                  unsigned* status, cudaStream_t s);
 
 struct IvfBuildArgs {
   int64_t kt, dt, cap;
@@ -262,9 +298,12 @@ cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t
                                const int32_t* term, const float* val32, int64_t* lens_then_ptr,
                                int32_t* mterm, double* mval, void* temp, cudaStream_t s, int phase);
 
-// Object-side preparation: norms, storage copy, global term ids, validation.
+// Object-side preparation: norms, storage copy, validation, and (term_rebase
+// = term, non-null) global term ids written in place; with term_rebase null
+// the rows are only read.
 cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local_max, const int64_t* row_ptr,
-                                   int32_t* term, const float* val32, void* val_store, int storage,
+                                   const int32_t* term, int32_t* term_rebase, const float* val32, void* val_store,
+                                   int storage,
                                    float* nx, int32_t n_inst, const int64_t* inst_docs,
                                    const int64_t* inst_toff, const int32_t* inst_terms, int validate,
                                    unsigned* status, unsigned* negative, cudaStream_t s);
@@ -299,6 +338,79 @@ struct TcHeadArgs {
   int num_sms;
 };
 cudaError_t launch_tc_head(const TcHeadArgs& h, cudaStream_t s);
+// The objects' tuples in term-major order, ascending object inside each term
+// (zeta): built once per object set by a stable sort of the CSR tuples by
+// term; the update step groups it by cluster, IVFD walks it per term.
+struct ZetaArgs {
+  int64_t n_docs, nnz, dt;
+  const int64_t* row_ptr;
+  const int32_t* term;
+  const float* val32;
+  int64_t* zptr;    // [D+1]
+  uint32_t* zterm;  // [nnz] term of each tuple
+  uint64_t* zov;    // [nnz] object << 32 | FP32 value bits
+  uint32_t* k32;    // [nnz] scratch keys
+  uint64_t* v64;    // [nnz] scratch payloads
+  void* temp;
+  const int64_t* d_nnz;
+  int tbits;        // bits of the (global) term ids
+};
+cudaError_t launch_build_zeta(const ZetaArgs& z, cudaStream_t s);
+
+// ------------------------------------------------------------------ IVFD
+// The comparison algorithm IVFD (Algorithm 4): objects also held as an
+// inverted file zeta (term-major (object, value) lists in ascending object),
+// assignment looping over the means (ivfd.cu).  FP32, one instance.
+constexpr int IVFD_SUB = 512;  // objects per sub-range (one warp's accumulator)
+struct IvfdArgs {
+  int64_t n_docs, nnz, dt;
+  int32_t k;
+  const int64_t* row_ptr;
+  const int32_t* term;
+  const float* val32;
+  const float* nx;
+  // zeta, built once per object set: zptr [D+1], zov [nnz] (object << 32 |
+  // value bits), zoff [D x (n_sub+1)] offset inside zeta_s of the first
+  // object >= r * IVFD_SUB
+  const int64_t* zptr;
+  const uint64_t* zov;
+  int32_t* zoff;
+  int64_t n_sub;
+  // the means, cluster-major FP64, and the inverted file's list bounds (for
+  // the zero-similarity test)
+  const int64_t* mptr;
+  const int32_t* mterm;
+  const double* mval;
+  const int64_t* term_ptr;
+  // per (chunk, object) top-2 of the chunk's means: [chunks x N]
+  int32_t chunks;
+  float* pbest;
+  float* psecond;
+  int32_t* pid;
+  // outputs and counters, as for the IVF kernel
+  int32_t* assign;
+  float* best;
+  float* gap;
+  float* err;
+  unsigned long long* entries;
+  unsigned long long* n_zero_sim;
+  int32_t rescore;
+  unsigned int* n_flagged;
+  int32_t* flag_obj;
+  int32_t* flag_cnt;
+  // near-ties: appended here (count *n_preflag) for an object-major IVF pass
+  // that collects their candidates; null = re-scored against every cluster
+  int32_t* preflag;
+  unsigned int* n_preflag;
+  int32_t nonneg;
+  const unsigned* negative;
+  const unsigned* means_negative;
+};
+int64_t ivfd_sub_ranges(int64_t n_docs);
+// zoff from zeta (zptr, zobj must be built).
+cudaError_t launch_build_ivfd_offsets(const IvfdArgs& a, cudaStream_t s);
+cudaError_t launch_assign_ivfd(const IvfdArgs& a, cudaStream_t s);
+
 // Transpose the dense head rows wd [rows x kpad] into wdT [kpad x ldt] (16-bit).
 cudaError_t launch_transpose16(const void* wd, int64_t rows, int64_t kpad, void* wdT, int64_t ldt, cudaStream_t s);
 cudaError_t launch_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsigned* status, cudaStream_t s);

@@ -163,18 +163,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_radix_hist(const K* keys, const 
 // block-local positions, stages keys and values in shared memory in digit
 // order, and then writes each digit's run with consecutive threads on
 // consecutive addresses (coalesced), at the run's global offset.
-template <typename K>
+template <typename K, typename V>
 __global__ void __launch_bounds__(RS_THREADS, RS_SCATTER_MIN_BLOCKS) k_radix_scatter(const K* __restrict__ kin,
-                                                              const uint32_t* __restrict__ vin,
-                                                              K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                              const V* __restrict__ vin,
+                                                              K* __restrict__ kout, V* __restrict__ vout,
                                                               const int64_t* d_n, int shift,
                                                               const uint32_t* __restrict__ offs, int64_t nb) {
   __shared__ uint32_t wcnt[RS_WARPS][RS_BINS];
   __shared__ uint32_t dbase[RS_BINS];   // global start of the block's run of digit d
   __shared__ uint32_t lbase[RS_BINS];   // block-local start of digit d
   extern __shared__ __align__(16) unsigned char rs_stage[];
-  K* sk = reinterpret_cast<K*>(rs_stage);
-  uint32_t* sv = reinterpret_cast<uint32_t*>(rs_stage + sizeof(K) * RS_TILE);
+  V* sv = reinterpret_cast<V*>(rs_stage);  // the wider type first: both stay aligned
+  K* sk = reinterpret_cast<K*>(rs_stage + sizeof(V) * RS_TILE);
   const int64_t n = *d_n;
   const int64_t base = (int64_t)blockIdx.x * RS_TILE;
   if (base >= n) return;  // uniform over the block
@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_SCATTER_MIN_BLOCKS) k_radix_sca
   for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += RS_THREADS) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   K k[RS_ROUNDS];
-  uint32_t v[RS_ROUNDS];
+  V v[RS_ROUNDS];
   uint32_t rk[RS_ROUNDS];
   const int64_t wbase = base + (int64_t)warp * (RS_ROUNDS * 32);
   const uint32_t lt_mask = (1u << lane) - 1u;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_SCATTER_MIN_BLOCKS) k_radix_sca
     const int64_t idx = wbase + r * 32 + lane;
     const bool valid = idx < n;
     k[r] = valid ? kin[idx] : K(0);
-    v[r] = valid ? vin[idx] : 0u;
+    v[r] = valid ? vin[idx] : V(0);
     const uint32_t d = valid ? ((uint32_t)(k[r] >> shift) & 255u) : 256u;
     const uint32_t peers = __match_any_sync(IVF_FULL_MASK, d);
     const uint32_t leader = __ffs(peers) - 1;
@@ -254,15 +254,15 @@ __global__ void __launch_bounds__(RS_THREADS, RS_SCATTER_MIN_BLOCKS) k_radix_sca
   }
 }
 
-template <typename K>
+template <typename K, typename V>
 constexpr size_t scatter_smem_bytes() {
-  return (sizeof(K) + sizeof(uint32_t)) * RS_TILE;
+  return (sizeof(K) + sizeof(V)) * RS_TILE;
 }
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-template <typename K>
-cudaError_t radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, const int64_t* d_n,
+template <typename K, typename V>
+cudaError_t radix_impl(K* keys, K* keys_alt, V* vals, V* vals_alt, const int64_t* d_n,
                        int64_t n_max, int bits, void* temp, cudaStream_t s, bool* in_alt) {
   int64_t nb = ceil_div(n_max, RS_TILE);
   if (nb < 1) nb = 1;
@@ -271,20 +271,20 @@ cudaError_t radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
   const int passes = (bits + 7) / 8;
   K* ki = keys;
   K* ko = keys_alt;
-  uint32_t* vi = vals;
-  uint32_t* vo = vals_alt;
+  V* vi = vals;
+  V* vo = vals_alt;
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
     k_radix_hist<K><<<(unsigned)nb, RS_THREADS, 0, s>>>(ki, d_n, shift, hist, nb);
     IVF_LAUNCH_CHECK();
     IVF_CU(exclusive_scan_u32(hist, hist, (int64_t)RS_BINS * nb, scan_tmp, s));
-    k_radix_scatter<K><<<(unsigned)nb, RS_THREADS, scatter_smem_bytes<K>(), s>>>(ki, vi, ko, vo, d_n, shift,
-                                                                                 hist, nb);
+    k_radix_scatter<K, V><<<(unsigned)nb, RS_THREADS, scatter_smem_bytes<K, V>(), s>>>(ki, vi, ko, vo, d_n,
+                                                                                       shift, hist, nb);
     IVF_LAUNCH_CHECK();
     K* tk = ki;
     ki = ko;
     ko = tk;
-    uint32_t* tv = vi;
+    V* tv = vi;
     vi = vo;
     vo = tv;
   }
@@ -295,10 +295,10 @@ cudaError_t radix_impl(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt,
 }  // namespace
 
 cudaError_t radix_prepare() {
-  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)scatter_smem_bytes<uint64_t>()));
-  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)scatter_smem_bytes<uint32_t>()));
+  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint32_t, uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)scatter_smem_bytes<uint32_t, uint32_t>()));
+  IVF_CU(cudaFuncSetAttribute(k_radix_scatter<uint32_t, uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)scatter_smem_bytes<uint32_t, uint64_t>()));
   return cudaSuccess;
 }
 
@@ -317,16 +317,16 @@ size_t radix_temp_bytes(int64_t n_max) {
   return align_up(((size_t)RS_BINS * nb + 1) * sizeof(uint32_t)) + scan_temp_bytes((int64_t)RS_BINS * nb);
 }
 
-cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
-                           const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
-                           bool* in_alt) {
-  return radix_impl<uint64_t>(keys, keys_alt, vals, vals_alt, d_n, n_max, bits, temp, s, in_alt);
-}
-
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                            const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
                            bool* in_alt) {
-  return radix_impl<uint32_t>(keys, keys_alt, vals, vals_alt, d_n, n_max, bits, temp, s, in_alt);
+  return radix_impl<uint32_t, uint32_t>(keys, keys_alt, vals, vals_alt, d_n, n_max, bits, temp, s, in_alt);
+}
+
+cudaError_t radix_sort_u32_wide(uint32_t* keys, uint32_t* keys_alt, uint64_t* vals, uint64_t* vals_alt,
+                                const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
+                                bool* in_alt) {
+  return radix_impl<uint32_t, uint64_t>(keys, keys_alt, vals, vals_alt, d_n, n_max, bits, temp, s, in_alt);
 }
 
 }  // namespace ivfk

@@ -1,8 +1,9 @@
 // Device-wide exclusive scan and stable LSD radix sort (key, uint32 payload).
 //
 // These are the counting-sort and prefix-sum building blocks of the update
-// step: grouping objects by cluster (the sets C_j of Algorithm 3), merging
-// member terms per cluster, and the term-major rebuild of the inverted file
+// step: grouping objects by cluster (the sets C_j of Algorithm 3), grouping
+// the objects' term-major tuples by cluster for the member sums, the
+// term-major copy of the objects itself, and the term-major rebuild of the inverted file
 // (Section 3: each posting list xi_s ascends in cluster id because a stable
 // sort by term keeps the cluster-major input order).
 #pragma once
@@ -26,11 +27,12 @@ cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void*
 // area; call it once per process (per device) before the first sort.
 size_t radix_temp_bytes(int64_t n_max);
 cudaError_t radix_prepare();
-cudaError_t radix_sort_u64(uint64_t* keys, uint64_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
-                           const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
-                           bool* in_alt);
 cudaError_t radix_sort_u32(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                            const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
                            bool* in_alt);
+// The same with 64-bit payloads (carried through every pass).
+cudaError_t radix_sort_u32_wide(uint32_t* keys, uint32_t* keys_alt, uint64_t* vals, uint64_t* vals_alt,
+                                const int64_t* d_n, int64_t n_max, int bits, void* temp, cudaStream_t s,
+                                bool* in_alt);
 
 }  // namespace ivfk

@@ -81,32 +81,49 @@ __global__ void k_member_out(UpdateArgs a, const uint32_t* keys, const uint32_t*
     a.cl_ptr[j] = lower_bound_dev<uint32_t>(keys, a.n_docs, (uint32_t)j);
 }
 
-// ------------------------------------------------------- A6 member sums
+// ---------------------------------------- the objects' tuples by term (zeta)
 
-// One warp per object: key (global cluster, global term), payload FP32 bits.
-__global__ void k_expand(UpdateArgs a) {
+// Warp per object: key = term, payload = (object << 32 | value bits).
+__global__ void k_zeta_keys(const ZetaArgs z, uint32_t* keys, uint64_t* vals) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = gw; i < a.n_docs; i += nw) {
-    const int b = a.n_inst > 1 ? find_inst<int64_t>(a.inst_docs, a.n_inst, i) : 0;
-    const uint64_t gc = (uint64_t)(a.inst_clu[b] + a.assign[i]);
-    // the instance's own term id: a cluster's terms all come from its instance
-    const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[b] : 0;
-    const int64_t r0 = a.row_ptr[i], r1 = a.row_ptr[i + 1];
-    for (int64_t h = r0 + lane; h < r1; h += 32) {
-      a.k64a[h] = (gc << a.tbits) | (uint64_t)(uint32_t)(a.term[h] - t0);
-      a.v32a[h] = __float_as_uint(a.val32[h]);
+  for (int64_t i = gw; i < z.n_docs; i += nw)
+    for (int64_t h = z.row_ptr[i] + lane; h < z.row_ptr[i + 1]; h += 32) {
+      keys[h] = (uint32_t)z.term[h];
+      vals[h] = ((uint64_t)i << 32) | (uint64_t)__float_as_uint(z.val32[h]);
     }
+}
+
+__global__ void k_zeta_ptr(const ZetaArgs z) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s <= z.dt; s += stride)
+    z.zptr[s] = lower_bound_dev<uint32_t>(z.zterm, z.nnz, (uint32_t)s);
+}
+
+// ------------------------------------------------------- A6 member sums
+
+// Key = global cluster of the tuple's object, payload = (term << 32 | value
+// bits).  A stable sort on this key alone orders the tuples by (cluster,
+// term, object): zeta is already in (term, object) order.
+__global__ void k_zc_keys(UpdateArgs a, uint32_t* keys, uint64_t* vals) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < a.nnz; q += stride) {
+    const uint64_t ov = a.zov[q];
+    const int64_t o = (int64_t)(ov >> 32);
+    const int b = a.n_inst > 1 ? find_inst<int64_t>(a.inst_docs, a.n_inst, o) : 0;
+    keys[q] = (uint32_t)(a.inst_clu[b] + a.assign[o]);
+    vals[q] = ((uint64_t)a.zterm[q] << 32) | (ov & 0xFFFFFFFFull);
   }
 }
 
-// After the scan, scanned[e+1] != scanned[e] marks the first entry of a run.
-__global__ void k_heads(const uint64_t* keys, const int64_t* d_n, uint32_t* flags) {
+// Run heads of (cluster, term) in that order; after the scan,
+// scanned[e+1] != scanned[e] marks the first entry of a run.
+__global__ void k_zc_heads(const uint32_t* cl, const uint64_t* tv, const int64_t* d_n, uint32_t* flags) {
   const int64_t n = *d_n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
-    flags[e] = (e == 0 || keys[e] != keys[e - 1]) ? 1u : 0u;
+    flags[e] = (e == 0 || cl[e] != cl[e - 1] || (tv[e] >> 32) != (tv[e - 1] >> 32)) ? 1u : 0u;
 }
 
 __global__ void k_starts(const uint32_t* scanned, const int64_t* d_n, uint32_t* starts, int64_t* d_u) {
@@ -120,17 +137,20 @@ __global__ void k_starts(const uint32_t* scanned, const int64_t* d_n, uint32_t* 
   }
 }
 
-// Each run of equal keys summed in FP64 in its (ascending object) order.
-__global__ void k_segsum(const uint64_t* keys, const uint32_t* vals, const uint32_t* starts, const int64_t* d_u,
-                         uint64_t* ukey, double* usum) {
-  const int64_t u_n = *d_u;
+// Each run of one (cluster, term) summed in FP64 in its (ascending object)
+// order; key (cluster, the term's id inside its instance: a cluster's terms
+// all come from its instance).
+__global__ void k_zc_segsum(const UpdateArgs a, const uint32_t* cl, const uint64_t* tv) {
+  const int64_t u_n = *a.d_u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
-    const uint32_t s0 = starts[u], s1 = starts[u + 1];
+    const uint32_t s0 = a.starts[u], s1 = a.starts[u + 1];
     double s = 0.0;
-    for (uint32_t e = s0; e < s1; ++e) s = __dadd_rn(s, (double)__uint_as_float(vals[e]));
-    ukey[u] = keys[s0];
-    usum[u] = s;
+    for (uint32_t e = s0; e < s1; ++e) s = __dadd_rn(s, (double)__uint_as_float((uint32_t)tv[e]));
+    const uint32_t gc = cl[s0];
+    const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc)] : 0;
+    a.ukey[u] = ((uint64_t)gc << a.tbits) | (uint64_t)(uint32_t)((int32_t)(tv[s0] >> 32) - t0);
+    a.usum[u] = s;
   }
 }
 
@@ -194,11 +214,11 @@ __global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
 }
 
 // Keep flags of the run sums (every nonzero sum), scanned into output ranks
-// by the caller; flags[u] for u < nnz (the scan writes the total at nnz).
-__global__ void k_keep_flags(UpdateArgs a) {
+// by the caller; flags[u] for u < u_max (the scan writes the total at u_max).
+__global__ void k_keep_flags(UpdateArgs a, int64_t u_max) {
   const int64_t u_n = *a.d_u;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < a.nnz; u += stride)
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_max; u += stride)
     a.flags[u] = (u < u_n && a.usum[u] != 0.0) ? 1u : 0u;
 }
 
@@ -427,7 +447,11 @@ __global__ void k_gather_copy(int64_t kt, const int32_t* doc_ids, const int64_t*
 // --------------------------------------------------------- objects
 
 template <typename WT>
-__global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_t* term, const float* val32,
+// term_rebase: the same array as term, written in place with global term ids
+// when an instance's term offset is non-zero; null = never written (the
+// caller's rows are read only).
+__global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, const int32_t* term,
+                                  int32_t* term_rebase, const float* val32,
                                   WT* val_store, float* nx, int32_t n_inst, const int64_t* inst_docs,
                                   const int64_t* inst_toff, const int32_t* inst_terms, int validate,
                                   unsigned* status, unsigned* negative) {
@@ -454,8 +478,8 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, int32_
       if (val_store) val_store[h] = from_f32<WT>(v);
     }
     __syncwarp();
-    if (toff != 0)
-      for (int64_t h = r0 + lane; h < r1; h += 32) term[h] = (int32_t)(term[h] + toff);
+    if (toff != 0 && term_rebase != nullptr)
+      for (int64_t h = r0 + lane; h < r1; h += 32) term_rebase[h] = (int32_t)(term[h] + toff);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(IVF_FULL_MASK, ss, o);
     const bool any_bad = __any_sync(IVF_FULL_MASK, bad);
@@ -480,7 +504,141 @@ __global__ void k_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsig
 
 }  // namespace
 
-cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
+// A7 from the run sums of A6 (ukey, usum, *d_u <= u_max): norms, new row
+// lengths, prefix sums, the normalised entries, kept rows of empty clusters.
+cudaError_t launch_means_from_sums(const UpdateArgs& a, int64_t u_max, cudaStream_t s) {
+  const unsigned gE = grid_for(u_max, T256, 16384);
+  const unsigned gK = grid_for(a.kt + 1, T256, 8192);
+  k_uptr<<<gK, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  k_cluster_norm<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
+  k_keep_flags<<<gE, T256, 0, s>>>(a, u_max);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_u32(a.flags, a.flags, u_max, a.temp, s));  // flags[u_max] <- total
+  k_write_entries<<<gE, T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  k_copy_kept<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+// ------------------------------------------ member sums gathered from shards
+
+__global__ void k_part_keys1(const PartialArgs p, uint32_t* keys, uint32_t* vals) {
+  const int64_t n = *p.d_n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    keys[e] = (uint32_t)p.term[e];
+    vals[e] = (uint32_t)e;
+  }
+}
+
+__global__ void k_part_keys2(const PartialArgs p, const uint32_t* perm1, uint32_t* keys, uint32_t* vals) {
+  const int64_t n = *p.d_n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const uint32_t q = perm1[e];
+    keys[e] = (uint32_t)p.cluster[q];
+    vals[e] = q;
+  }
+}
+
+__global__ void k_part_heads(const PartialArgs p, const uint32_t* perm, uint32_t* flags) {
+  const int64_t n = *p.d_n;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    bool head = e == 0;
+    if (!head) {
+      const uint32_t q = perm[e], r = perm[e - 1];
+      head = p.cluster[q] != p.cluster[r] || p.term[q] != p.term[r];
+    }
+    flags[e] = head ? 1u : 0u;
+  }
+}
+
+// Run sums in the given (shard) order; key (cluster, term) as A6 makes it.
+__global__ void k_part_segsum(const UpdateArgs a, const PartialArgs p, const uint32_t* perm) {
+  const int64_t u_n = *a.d_u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
+    const uint32_t s0 = a.starts[u], s1 = a.starts[u + 1];
+    double s = 0.0;
+    for (uint32_t e = s0; e < s1; ++e) s = __dadd_rn(s, p.sum[perm[e]]);
+    const uint32_t q = perm[s0];
+    a.ukey[u] = ((uint64_t)(uint32_t)p.cluster[q] << a.tbits) | (uint64_t)(uint32_t)p.term[q];
+    a.usum[u] = s;
+  }
+}
+
+__global__ void k_part_out(const UpdateArgs a, int32_t* cluster, int32_t* term, double* sum) {
+  const int64_t u_n = *a.d_u;
+  const uint64_t tmask = (1ull << a.tbits) - 1ull;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
+    const uint64_t k = a.ukey[u];
+    cluster[u] = (int32_t)(k >> a.tbits);
+    term[u] = (int32_t)(k & tmask);
+    sum[u] = a.usum[u];
+  }
+}
+
+__global__ void k_check_partials(int64_t n, const int32_t* cluster, const int32_t* term, int32_t k, int32_t d,
+                                 unsigned* status) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride)
+    bad |= cluster[e] < 0 || cluster[e] >= k || term[e] < 0 || term[e] >= d;
+  if (__any_sync(IVF_FULL_MASK, bad) && (threadIdx.x & 31) == 0) atomicOr(status, (unsigned)STS_BAD_ROWS);
+}
+
+cudaError_t launch_check_partials(int64_t n, const int32_t* cluster, const int32_t* term, int32_t k, int32_t d,
+                                  unsigned* status, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_check_partials<<<grid_for(n, T256, 8192), T256, 0, s>>>(n, cluster, term, k, d, status);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_partial_out(const UpdateArgs& a, int64_t u_max, int32_t* cluster, int32_t* term, double* sum,
+                               cudaStream_t s) {
+  k_part_out<<<grid_for(u_max, T256, 16384), T256, 0, s>>>(a, cluster, term, sum);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
+}
+
+cudaError_t launch_update_from_partials(const UpdateArgs& a, const PartialArgs& p, cudaStream_t s) {
+  const unsigned gP = grid_for(p.n_max, T256, 16384);
+  uint32_t* ka = reinterpret_cast<uint32_t*>(a.k64a);
+  uint32_t* kb = reinterpret_cast<uint32_t*>(a.k64b);
+  // stable by term, then stably by cluster: (cluster, term) order, equal keys in shard order
+  k_part_keys1<<<gP, T256, 0, s>>>(p, ka, a.v32a);
+  IVF_LAUNCH_CHECK();
+  bool alt = false;
+  IVF_CU(radix_sort_u32(ka, kb, a.v32a, a.v32b, p.d_n, p.n_max, a.tbits, a.temp, s, &alt));
+  const uint32_t* perm1 = alt ? a.v32b : a.v32a;
+  uint32_t* k2 = alt ? ka : kb;
+  uint32_t* v2 = alt ? a.v32a : a.v32b;
+  k_part_keys2<<<gP, T256, 0, s>>>(p, perm1, k2, v2);
+  IVF_LAUNCH_CHECK();
+  bool alt2 = false;
+  uint32_t* k2b = alt ? kb : ka;
+  uint32_t* v2b = alt ? a.v32b : a.v32a;
+  IVF_CU(radix_sort_u32(k2, k2b, v2, v2b, p.d_n, p.n_max, a.kbits, a.temp, s, &alt2));
+  const uint32_t* perm = alt2 ? v2b : v2;
+  k_part_heads<<<gP, T256, 0, s>>>(p, perm, a.flags);
+  IVF_LAUNCH_CHECK();
+  IVF_CU(exclusive_scan_u32(a.flags, a.flags, p.n_max, a.temp, s));
+  k_starts<<<gP, T256, 0, s>>>(a.flags, p.d_n, a.starts, a.d_u);
+  IVF_LAUNCH_CHECK();
+  k_part_segsum<<<gP, T256, 0, s>>>(a, p, perm);
+  IVF_LAUNCH_CHECK();
+  return launch_means_from_sums(a, p.n_max, s);
+}
+
+// A5 (members) and A6 (run sums per (cluster, term)).
+cudaError_t launch_member_sums(const UpdateArgs& a, cudaStream_t s) {
   const unsigned gN = grid_for(a.n_docs, T256, 8192);
   // A5: C_j as a stable counting sort of objects by cluster
   k_member_keys<<<gN, T256, 0, s>>>(a);
@@ -494,34 +652,43 @@ cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
         a, alt ? kb : ka, alt ? a.v32b : a.v32a);
     IVF_LAUNCH_CHECK();
   }
-  // A6: (cluster, term) keys in object order, stable sort, FP64 run sums
-  k_expand<<<grid_for(a.n_docs * 32, T256, 16384), T256, 0, s>>>(a);
+  // A6: zeta's tuples stably sorted by cluster alone -- (cluster, term,
+  // object) order -- then FP64 run sums per (cluster, term)
+  const unsigned gE = grid_for(a.nnz, T256, 16384);
+  k_zc_keys<<<gE, T256, 0, s>>>(a, a.v32a, a.k64a);
   IVF_LAUNCH_CHECK();
   bool alt = false;
-  IVF_CU(radix_sort_u64(a.k64a, a.k64b, a.v32a, a.v32b, a.d_nnz, a.nnz, a.kbits + a.tbits, a.temp, s, &alt));
-  const uint64_t* keys = alt ? a.k64b : a.k64a;
-  const uint32_t* vals = alt ? a.v32b : a.v32a;
-  const unsigned gE = grid_for(a.nnz, T256, 16384);
-  k_heads<<<gE, T256, 0, s>>>(keys, a.d_nnz, a.flags);
+  IVF_CU(radix_sort_u32_wide(a.v32a, a.v32b, a.k64a, a.k64b, a.d_nnz, a.nnz, a.kbits, a.temp, s, &alt));
+  const uint32_t* cl = alt ? a.v32b : a.v32a;
+  const uint64_t* tv = alt ? a.k64b : a.k64a;
+  k_zc_heads<<<gE, T256, 0, s>>>(cl, tv, a.d_nnz, a.flags);
   IVF_LAUNCH_CHECK();
   IVF_CU(exclusive_scan_u32(a.flags, a.flags, a.nnz, a.temp, s));
   k_starts<<<gE, T256, 0, s>>>(a.flags, a.d_nnz, a.starts, a.d_u);
   IVF_LAUNCH_CHECK();
-  k_segsum<<<gE, T256, 0, s>>>(keys, vals, a.starts, a.d_u, a.ukey, a.usum);
+  k_zc_segsum<<<gE, T256, 0, s>>>(a, cl, tv);
   IVF_LAUNCH_CHECK();
-  // A7: norms, new row lengths, prefix sums, write
-  const unsigned gK = grid_for(a.kt + 1, T256, 8192);
-  k_uptr<<<gK, T256, 0, s>>>(a);
+  return cudaSuccess;
+}
+
+cudaError_t launch_update_means(const UpdateArgs& a, cudaStream_t s) {
+  IVF_CU(launch_member_sums(a, s));
+  return launch_means_from_sums(a, a.nnz, s);  // A7
+}
+
+cudaError_t launch_build_zeta(const ZetaArgs& z, cudaStream_t s) {
+  // a stable sort by term of (term, object|value); the passes ping-pong
+  // between the scratch pair and zeta itself, started so the result lands in zeta
+  const int passes = (z.tbits + 7) / 8;
+  uint32_t* k0 = (passes & 1) ? z.k32 : z.zterm;
+  uint32_t* k1 = (passes & 1) ? z.zterm : z.k32;
+  uint64_t* v0 = (passes & 1) ? z.v64 : z.zov;
+  uint64_t* v1 = (passes & 1) ? z.zov : z.v64;
+  k_zeta_keys<<<grid_for(z.n_docs * 32, T256, 16384), T256, 0, s>>>(z, k0, v0);
   IVF_LAUNCH_CHECK();
-  k_cluster_norm<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
-  IVF_LAUNCH_CHECK();
-  IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
-  k_keep_flags<<<gE, T256, 0, s>>>(a);
-  IVF_LAUNCH_CHECK();
-  IVF_CU(exclusive_scan_u32(a.flags, a.flags, a.nnz, a.temp, s));  // flags[nnz] <- total
-  k_write_entries<<<gE, T256, 0, s>>>(a);
-  IVF_LAUNCH_CHECK();
-  k_copy_kept<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
+  bool alt = false;
+  IVF_CU(radix_sort_u32_wide(k0, k1, v0, v1, z.d_nnz, z.nnz, z.tbits, z.temp, s, &alt));
+  k_zeta_ptr<<<grid_for(z.dt + 1, T256, 16384), T256, 0, s>>>(z);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
 }
@@ -616,7 +783,7 @@ cudaError_t launch_gather_rows(int64_t kt, const int32_t* doc_ids, const int64_t
 }
 
 cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local_max, const int64_t* row_ptr,
-                                   int32_t* term, const float* val32, void* val_store, int storage, float* nx,
+                                   const int32_t* term, int32_t* term_rebase, const float* val32, void* val_store, int storage, float* nx,
                                    int32_t n_inst, const int64_t* inst_docs, const int64_t* inst_toff,
                                    const int32_t* inst_terms, int validate, unsigned* status, unsigned* negative,
                                    cudaStream_t s) {
@@ -625,18 +792,18 @@ cudaError_t launch_prepare_objects(int64_t n_docs, int64_t nnz, int64_t dt_local
   const unsigned g = grid_for(n_docs * 32, T256, 16384);
   switch (storage) {
     case ST_F16:
-      k_prepare_objects<__half><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, static_cast<__half*>(val_store), nx,
+      k_prepare_objects<__half><<<g, T256, 0, s>>>(n_docs, row_ptr, term, term_rebase, val32, static_cast<__half*>(val_store), nx,
                                                    n_inst, inst_docs, inst_toff, inst_terms, validate, status,
                                                    negative);
       break;
     case ST_BF16:
-      k_prepare_objects<__nv_bfloat16><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32,
+      k_prepare_objects<__nv_bfloat16><<<g, T256, 0, s>>>(n_docs, row_ptr, term, term_rebase, val32,
                                                           static_cast<__nv_bfloat16*>(val_store), nx, n_inst,
                                                           inst_docs, inst_toff, inst_terms, validate, status,
                                                           negative);
       break;
     default:
-      k_prepare_objects<float><<<g, T256, 0, s>>>(n_docs, row_ptr, term, val32, nullptr, nx, n_inst, inst_docs,
+      k_prepare_objects<float><<<g, T256, 0, s>>>(n_docs, row_ptr, term, term_rebase, val32, nullptr, nx, n_inst, inst_docs,
                                                   inst_toff, inst_terms, validate, status, negative);
       break;
   }

@@ -30,16 +30,18 @@ IVF_FLAG_SPARSE_ONLY = 8
 IVF_FLAG_TENSOR_HEAD = 16
 IVF_FLAG_TILE_MAJOR = 32
 IVF_FLAG_OBJECT_MAJOR = 64
+IVF_FLAG_IVFD = 128
 SCHEDULE_FLAGS = {"auto": 0, "tile_major": IVF_FLAG_TILE_MAJOR, "object_major": IVF_FLAG_OBJECT_MAJOR}
 KERNEL_FLAGS = {"auto": 0, "dense_head": IVF_FLAG_DENSE_HEAD, "sparse": IVF_FLAG_SPARSE_ONLY,
-                "tensor_head": IVF_FLAG_TENSOR_HEAD}
+                "tensor_head": IVF_FLAG_TENSOR_HEAD, "ivfd": IVF_FLAG_IVFD}
 
 # Every symbol include/ivf.h declares.
 EXPORTS = ["ivf_create", "ivf_load_objects", "ivf_set_means", "ivf_set_means_from_docs", "ivf_assign",
            "ivf_update", "ivf_iterate", "ivf_get_assign", "ivf_get_best", "ivf_get_gap", "ivf_get_info",
            "ivf_get_err_bound", "ivf_get_means", "ivf_get_inverted_file", "ivf_get_members", "ivf_set_assign", "ivf_restore_means",
            "ivf_last_error", "ivf_destroy", "ivf_launch_count", "ivf_version", "ivfb_create", "ivfb_get_changed",
-           "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static", "ivf_probe_l2_read", "ivf_head_product"]
+           "ivf_timing_reset", "ivf_get_timing", "ivf_assign_static", "ivf_probe_l2_read", "ivf_head_product",
+           "ivf_get_partial_sums", "ivf_update_from_partials"]
 IVF_STATIC_MAX_DOCS = 16384
 IVF_STATIC_MAX_K = 12288
 
@@ -134,6 +136,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "ivf_assign_static": ([i64, vp, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], st),
         "ivf_probe_l2_read": ([i64, i32, vp, ctypes.POINTER(ctypes.c_double)], st),
         "ivf_head_product": ([i64, i32, i32, vp, i64, vp, i64, vp, i64, i32, vp], st),
+        "ivf_get_partial_sums": ([vp, i64, vp, vp, vp, ctypes.POINTER(i64)], st),
+        "ivf_update_from_partials": ([vp, i64, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -209,7 +213,9 @@ class IVF:
     "f16" or "bf16" (the streamed value type; accumulation is FP32, near-ties
     are re-scored in FP64 when ``rescore``); ``kernel`` restricts the
     autotuner to one family -- "auto", "sparse", "dense_head" (CUDA-core dense
-    rows) or "tensor_head" (FP16/BF16: dense rows as a tensor-core GEMM);
+    rows), "tensor_head" (FP16/BF16: dense rows as a tensor-core GEMM) or
+    "ivfd" (the comparison algorithm IVFD: Algorithm 4's loop order over an
+    inverted file of the objects);
     ``schedule`` restricts it to "tile_major" (one launch per cluster tile
     over all objects) or "object_major" shapes (default "auto": either);
     ``k_tile`` / ``warps_per_block`` fix the launch shape instead of tuning
@@ -343,6 +349,29 @@ class IVF:
         a = np.empty(self.n_docs, dtype=np.float32)
         self._check(self._lib.ivf_get_gap(self._ctx, a.ctypes.data))
         return a
+
+    def get_partial_sums(self):
+        """This context's member sums of its last assignment, before
+        normalisation: (cluster int32[U], term int32[U], sum float64[U]) in
+        ascending (cluster, term) (ivf_get_partial_sums)."""
+        n = ctypes.c_int64(0)
+        self._check(self._lib.ivf_get_partial_sums(self._ctx, 0, None, None, None, ctypes.byref(n)))
+        u = int(n.value)
+        cl = np.empty(u, dtype=np.int32)
+        tm = np.empty(u, dtype=np.int32)
+        sm = np.empty(u, dtype=np.float64)
+        if u:
+            self._check(self._lib.ivf_get_partial_sums(self._ctx, u, cl.ctypes.data, tm.ctypes.data, sm.ctypes.data,
+                                                       ctypes.byref(n)))
+        return cl, tm, sm
+
+    def update_from_partials(self, cluster, term, sums) -> None:
+        """The update step from member sums of every shard, concatenated in
+        shard order (ivf_update_from_partials)."""
+        cp, ck = _ptr(cluster, np.int32)
+        tp, tk = _ptr(term, np.int32)
+        sp, sk = _ptr(sums, np.float64)
+        self._check(self._lib.ivf_update_from_partials(self._ctx, int(len(cluster)), cp, tp, sp))
 
     def get_err_bound(self) -> np.ndarray:
         """Per object: a bound on |best - rho| against the FP64 means (ivf_get_err_bound)."""

@@ -1,6 +1,5 @@
 """bench.py's host-side helpers (CPU only): the roofline's traffic and peak
 sources, and the ClockSampler's verdict on a clock record."""
-import hashlib
 import json
 
 import bench
@@ -8,12 +7,12 @@ import bench
 
 def _traffic_file(tmp_path, sha, workload, value=123456789):
     p = tmp_path / "traffic.txt"
-    p.write_text(f"# comment\nassign_cu_sha256: {sha}\nworkload: {workload}\nbytes_per_launch[f32]: {value}\n")
+    p.write_text(f"# comment\nassign_src_sha256: {sha}\nworkload: {workload}\nbytes_per_launch[f32]: {value}\n")
     return str(p)
 
 
 def test_traffic_only_for_the_unchanged_kernel_and_the_same_workload(tmp_path, monkeypatch):
-    sha = hashlib.sha256(open(bench.ASSIGN_SRC, "rb").read()).hexdigest()
+    sha = bench.assign_sources_sha()
     monkeypatch.setattr(bench, "TRAFFIC_FILE", _traffic_file(tmp_path, sha, "wl-a"))
     assert bench.traffic_per_launch("wl-a", "f32") == 123456789.0
     assert bench.traffic_per_launch("wl-b", "f32") is None      # other workload
@@ -25,9 +24,9 @@ def test_traffic_only_for_the_unchanged_kernel_and_the_same_workload(tmp_path, m
 
 
 def test_traffic_of_the_schedule_in_use_and_l2_bytes(tmp_path, monkeypatch):
-    sha = hashlib.sha256(open(bench.ASSIGN_SRC, "rb").read()).hexdigest()
+    sha = bench.assign_sources_sha()
     p = tmp_path / "traffic.txt"
-    p.write_text(f"assign_cu_sha256: {sha}\nworkload: wl\nschedule[f32]: tile_major\n"
+    p.write_text(f"assign_src_sha256: {sha}\nworkload: wl\nschedule[f32]: tile_major\n"
                  "bytes_per_launch[f32]: 1000\nl2_bytes_per_launch[f32]: 5000\n")
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(p))
     assert bench.traffic_per_launch("wl", "f32", "tile_major") == 1000.0
@@ -39,7 +38,7 @@ def test_committed_traffic_file_parses():
     """The committed summary names a workload and an FP32 byte count; whether
     it applies is decided at run time by the kernel source's hash."""
     text = open(bench.TRAFFIC_FILE).read()
-    assert "assign_cu_sha256:" in text and "workload:" in text and "bytes_per_launch[f32]:" in text
+    assert "assign_src_sha256:" in text and "workload:" in text and "bytes_per_launch[f32]:" in text
 
 
 def test_peaks_measured_then_fallback(tmp_path, monkeypatch):

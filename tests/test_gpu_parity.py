@@ -824,7 +824,8 @@ def test_tensor_head_needs_16bit_storage():
 
 
 @pytest.mark.parametrize("kernel,k_tile,storage", [("dense_head", 2048, "f32"), ("dense_head", 1024, "f32"),
-                                                   ("sparse", 512, "f32"), ("dense_head", 2048, "bf16")])
+                                                   ("sparse", 512, "f32"), ("dense_head", 2048, "bf16"),
+                                                   ("tensor_head", 2048, "bf16"), ("tensor_head", 1024, "f16")])
 def test_tile_major_equals_object_major(kernel, k_tile, storage):
     """One launch per cluster tile over all objects, with (best, id, second)
     carried in device memory, sums every rho_c in the same order as the
@@ -861,3 +862,48 @@ def test_tile_major_equals_object_major(kernel, k_tile, storage):
     for rep in lockstep(c, k, None, 2, means_rows=rows, kernel=kernel, k_tile=k_tile, schedule="tile_major",
                         storage=storage, best_tol=1e-5 if storage == "f32" else 2.5e-2):
         assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("k", [37, 700, 3000])
+def test_ivfd_equals_sparse_ivf(k):
+    """IVFD (Algorithm 4: the objects as an inverted file, the assignment
+    looping over the means) multiplies the same posting entries as IVF (Eq. 15)
+    and sums every rho_c in the same ascending term order, so without the
+    re-score its FP32 results equal the sparse IVF kernel's bit for bit; with
+    it, the lockstep check against the FP64 oracle holds."""
+    c = corpus_for(5000, 4000, mean_len=40.0, seed=k, kind="lognormal", lo=3, hi=300)
+    ids = dg.init_doc_ids(c.n_docs, k, k)
+    out = {}
+    for kernel in ("sparse", "ivfd"):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel=kernel, rescore=False) as m:
+            m.set_means_from_docs(ids)
+            sts = [m.assign()]
+            m.update()
+            sts.append(m.assign())
+            out[kernel] = (m.get_assign(), m.get_best(), m.get_gap(), [s["entries_visited"] for s in sts],
+                           [s["n_zero_sim"] for s in sts])
+    for x, y in zip(out["ivfd"][:3], out["sparse"][:3]):
+        assert np.array_equal(np.asarray(x).view(np.uint32), np.asarray(y).view(np.uint32))
+    assert out["ivfd"][3] == out["sparse"][3] and out["ivfd"][4] == out["sparse"][4]
+    for rep in lockstep(c, k, ids, 3, kernel="ivfd"):
+        assert_report_ok(rep)
+
+
+def test_ivfd_object_reload_and_unsupported_forms():
+    """The object inverted file follows ivf_load_objects; FP16/BF16 storage is
+    not offered for IVFD."""
+    c = corpus_for(3000, 3000, mean_len=30.0, seed=77)
+    k = 150
+    ids = dg.init_doc_ids(c.n_docs, k, 77)
+    flip = np.where(np.random.default_rng(77).random(c.nnz) < 0.3, -c.val, c.val).astype(np.float32)
+    res = {}
+    for kernel in ("sparse", "ivfd"):
+        with ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel=kernel) as m:
+            m.set_means_from_docs(ids)
+            m.iterate(2)
+            m.load_objects(c.row_ptr, c.term, flip)
+            m.assign()
+            res[kernel] = m.get_assign()
+    assert np.array_equal(res["ivfd"], res["sparse"])
+    with pytest.raises(ivf.IvfError):
+        ivf.IVF(c.row_ptr, c.term, c.val, c.n_terms, k, kernel="ivfd", storage="bf16")
