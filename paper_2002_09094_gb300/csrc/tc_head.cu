@@ -10,17 +10,19 @@
 // the 5th-generation tensor cores:
 //   * A = x_h (batch x T, K-major) and B = w_h (kpad x T, K-major), 16-bit,
 //     staged into shared memory by TMA (cp.async.bulk.tensor, 128-byte
-//     swizzle) through a 4-stage mbarrier ring;
+//     swizzle) through a 3-stage mbarrier ring of 256-object x 64-slot A
+//     tiles and 256-cluster x 64-slot B tiles;
 //   * one elected thread issues tcgen05.mma (M = 128 objects, N = 256
-//     clusters, K = 16 per instruction) into an FP32 accumulator in TMEM;
-//     two accumulators (512 TMEM columns) let the epilogue of one tile
-//     overlap the MMAs of the next;
-//   * four epilogue warps read the accumulator with tcgen05.ld and store it
-//     in the storage type (the assignment kernel adds the sparse tail and
-//     takes the argmax);
-//   * a K-chunk of 64 head slots that is zero for all 128 objects of a tile
-//     (flags from the kernel that builds x_h) is neither loaded nor
-//     multiplied;
+//     clusters, K = 16 per instruction) for both 128-object halves of the
+//     256-object tile against the same B stage -- half the B traffic per
+//     flop of a 128-object tile -- into two FP32 accumulators in TMEM (512
+//     columns);
+//   * eight epilogue warps read the accumulators with tcgen05.ld and store
+//     them in the storage type (the assignment kernel adds the sparse tail
+//     and takes the argmax);
+//   * a K-chunk of 64 head slots that is zero for all 256 objects of a tile
+//     (flags from the kernel that builds x_h, per 128 objects) is neither
+//     loaded nor multiplied;
 //   * persistent grid, one CTA per SM, tiles in bands of 32 object blocks so
 //     that a band's A rows and the B slices in use stay in L2.
 // Every wait on an mbarrier is bounded (about two seconds of the global
@@ -41,16 +43,19 @@ namespace ivfk {
 
 namespace {
 
-constexpr int BM = 128;  // objects per tile = TMEM lanes
-constexpr int BN = 256;  // clusters per tile = TMEM columns of one accumulator
-constexpr int BK = 64;   // head slots per stage: 128 bytes of 16-bit values = one swizzle row
-constexpr int STAGES = 4;
-constexpr int UK = 16;   // K of one tcgen05.mma for 16-bit operands
+constexpr int HM = 128;      // objects per MMA = TMEM lanes
+constexpr int BM = 2 * HM;   // objects per tile: two MMA halves over one B stage
+constexpr int BN = 256;      // clusters per tile = TMEM columns of one accumulator
+constexpr int BK = 64;       // head slots per stage: 128 bytes of 16-bit values = one swizzle row
+constexpr int STAGES = 3;
+constexpr int UK = 16;       // K of one tcgen05.mma for 16-bit operands
 constexpr int A_BYTES = BM * BK * 2;
+constexpr int A_HALF_BYTES = HM * BK * 2;
 constexpr int B_BYTES = BN * BK * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 2 * BN;
-constexpr int THREADS = 192;  // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int TMEM_COLS = 2 * BN;  // accumulator of half h at columns h * BN
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int BAND = 32;      // object blocks per band of the tile order
 constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + 256;
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
@@ -62,7 +67,7 @@ struct TcArgs {
   uint16_t* d;              // [m x ldd] in the storage type
   int64_t ldd;
   uint32_t idesc;           // instruction descriptor
-  const uint8_t* chunk_nz;  // [ceil(m / BM) x k / BK] nonzero flags, or null (all chunks)
+  const uint8_t* chunk_nz;  // [ceil(m / HM) x k / BK] nonzero flags per 128 objects, or null (all chunks)
   unsigned* status;
 };
 
@@ -173,8 +178,12 @@ __device__ __forceinline__ void tile_coords(int64_t t, int m_blocks, int n_block
   *nb = (int)(r / rows);
 }
 
+// chunk kc of 256-object tile mb holds a value (either 128-object half)
 __device__ __forceinline__ bool chunk_live(const TcArgs& a, int mb, int kc, int kchunks) {
-  return a.chunk_nz == nullptr || a.chunk_nz[(int64_t)mb * kchunks + kc] != 0;
+  if (a.chunk_nz == nullptr) return true;
+  const int64_t h0 = 2 * (int64_t)mb;
+  const int64_t nh = (a.m + HM - 1) / HM;
+  return a.chunk_nz[h0 * kchunks + kc] != 0 || (h0 + 1 < nh && a.chunk_nz[(h0 + 1) * kchunks + kc] != 0);
 }
 
 template <bool BF16>
@@ -197,11 +206,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* sa = smem;
   uint8_t* sb = smem + STAGES * A_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], drain
+  // full[STAGES], empty[STAGES], acc_full, acc_empty, drain
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t accf0 = smem_u32(bars + 2 * STAGES), acce0 = smem_u32(bars + 2 * STAGES + 2);
-  const uint32_t drain = smem_u32(bars + 2 * STAGES + 4);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  const uint32_t accf = smem_u32(bars + 2 * STAGES), acce = smem_u32(bars + 2 * STAGES + 1);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 2);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -213,10 +222,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    for (int q = 0; q < 2; ++q) {
-      mbar_init(accf0 + 8 * q, 1);
-      mbar_init(acce0 + 8 * q, 4);  // one arrival per epilogue warp
-    }
+    mbar_init(accf, 1);
+    mbar_init(acce, EPI_WARPS);  // one arrival per epilogue warp
     mbar_init(drain, 1);
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -274,14 +281,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
       uint32_t stage = 0, phase = 0;
-      uint32_t acc = 0, acc_phase = 0;
+      uint32_t acc_phase = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
         int mb, nb;
         tile_coords(t, m_blocks, n_blocks, &mb, &nb);
-        if (!mbar_wait(acce0 + 8 * acc, acc_phase ^ 1u, abort)) break;
+        if (!mbar_wait(acce, acc_phase ^ 1u, abort)) break;  // the epilogue has drained the accumulators
         fence_after_sync();
-        const uint32_t d_tmem = tmem + acc * BN;
         uint32_t accumulate = 0;
         for (int kc = 0; kc < kchunks; ++kc) {
           if (!chunk_live(a, mb, kc, kchunks)) continue;
@@ -293,7 +299,9 @@ __global__ void __launch_bounds__(THREADS, 1)
           const uint32_t a0 = smem_u32(sa + stage * A_BYTES), b0 = smem_u32(sb + stage * B_BYTES);
 #pragma unroll
           for (int kk = 0; kk < BK / UK; ++kk) {
-            umma(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0 + kk * UK * 2), a.idesc, accumulate);
+            const uint64_t bd = sw128_desc(b0 + kk * UK * 2);
+            umma(tmem, sw128_desc(a0 + kk * UK * 2), bd, a.idesc, accumulate);
+            umma(tmem + BN, sw128_desc(a0 + A_HALF_BYTES + kk * UK * 2), bd, a.idesc, accumulate);
             accumulate = 1;
           }
           umma_commit(empty0 + 8 * stage);  // the stage is free once these MMAs have read it
@@ -303,11 +311,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
         }
         if (!ok) break;
-        umma_commit(accf0 + 8 * acc);  // accumulator complete (immediately when no chunk was live)
-        if (++acc == 2) {
-          acc = 0;
-          acc_phase ^= 1u;
-        }
+        umma_commit(accf);  // accumulators complete (immediately when no chunk was live)
+        acc_phase ^= 1u;
       }
       // every MMA issued has finished before the TMEM is freed
       umma_commit(drain);
@@ -315,14 +320,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       while (!mbar_try_wait(drain, 0) && now_ns() - t0 < WAIT_NS) {
       }
     }
-  } else {  // epilogue: warps 2-5, TMEM lane quarter warp % 4
+  } else {  // epilogue: warps 2-9; TMEM lane quarter warp % 4, M half (warp - 2) / 4
     const int q = warp & 3;
-    const int row = q * 32 + lane;
-    uint32_t acc = 0, acc_phase = 0;
+    const int half = (warp - 2) >> 2;
+    const int row = half * HM + q * 32 + lane;
+    uint32_t acc_phase = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
       int mb, nb;
       tile_coords(t, m_blocks, n_blocks, &mb, &nb);
-      if (!mbar_wait(accf0 + 8 * acc, acc_phase, abort)) break;
+      if (!mbar_wait(accf, acc_phase, abort)) break;
       fence_after_sync();
       bool live = a.chunk_nz == nullptr;
       for (int kc = 0; kc < kchunks && !live; ++kc) live = chunk_live(a, mb, kc, kchunks);
@@ -332,7 +338,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int c = 0; c < BN; c += 32) {
         uint32_t v[32];
         if (live) {
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * BN + c, v);
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + half * BN + c, v);
         } else {
 #pragma unroll
           for (int j = 0; j < 32; ++j) v[j] = 0u;
@@ -347,11 +353,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       fence_before_sync();
       __syncwarp();
-      if (lane == 0) mbar_arrive(acce0 + 8 * acc);
-      if (++acc == 2) {
-        acc = 0;
-        acc_phase ^= 1u;
-      }
+      if (lane == 0) mbar_arrive(acce);
+      acc_phase ^= 1u;
     }
   }
   fence_before_sync();
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28.
 uint32_t make_idesc(bool bf16) {
   const uint32_t ab = bf16 ? 1u : 0u;
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(HM >> 4) << 24);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
