@@ -626,6 +626,8 @@ IvfBuildArgs ivf_args(ivf_ctx* c, int mb) {
   a.k32b = reinterpret_cast<uint32_t*>(c->k64b);
   a.v32a = c->v32a;
   a.v32b = c->v32b;
+  a.v64a = c->k64a;
+  a.v64b = c->k64b;
   a.temp = c->temp;
   a.status = &c->dc->status;
   if (c->shape.head_r > 0 && c->head_slot) {
@@ -1245,7 +1247,10 @@ ivf_status autotune(ivf_ctx* c) {
     // tensor-core head: 16-bit storage, one instance, K over one 1,024-cluster tile
     const bool tc_ok = !no_head && c->cfg.storage != IVF_F32 && c->n_inst == 1 && c->kmax > 32 * HEAD_R_LARGE;
     if (tc_ok && (tc_only || !(c->cfg.flags & IVF_FLAG_DENSE_HEAD)))  // DENSE_HEAD: the CUDA-core head
-      for (int sub : {1, 2})
+      // shared-memory tiles of 1-8 head sub-tiles: wider tiles read each
+      // object's terms and their list offsets in fewer passes, at fewer
+      // resident warps
+      for (int sub : {1, 2, 4, 8})
         for (float theta : {0.5f, 0.25f, 0.125f, 0.0625f})
           for (int wp : {4, 8})
             if (shape_for(c, c->kmax, 0, wp, &sh, HEAD_R_LARGE, theta, sub, true)) cands.push_back(sh);
@@ -1434,7 +1439,9 @@ ivf_status enqueue_assign(ivf_ctx* c, int target, int prev, bool timed = false) 
     r.err = c->errb;
     r.nx = c->nx;
     r.n_rescored = &c->dc->n_rescored;
-    CK(c, launch_rescore(r, 2 * c->num_sms, s));
+    // one warp per flagged object, latency bound: a full GPU of warps (8
+    // blocks of 8 warps per SM) keeps enough FP64 dot products in flight
+    CK(c, launch_rescore(r, 8 * c->num_sms, s));
   }
   ReduceArgs ra{};
   ra.n_docs = c->N;

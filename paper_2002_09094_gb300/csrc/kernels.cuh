@@ -279,6 +279,8 @@ struct IvfBuildArgs {
   uint32_t* k32b;
   uint32_t* v32a;
   uint32_t* v32b;
+  uint64_t* v64a;  // [cap] payloads of the rebuild sort
+  uint64_t* v64b;
   void* temp;
   unsigned* status;
 };

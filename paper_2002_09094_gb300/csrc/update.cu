@@ -213,43 +213,49 @@ __global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
   }
 }
 
-// Keep flags of the run sums (every nonzero sum), scanned into output ranks
-// by the caller; flags[u] for u < u_max (the scan writes the total at u_max).
-__global__ void k_keep_flags(UpdateArgs a, int64_t u_max) {
-  const int64_t u_n = *a.d_u;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_max; u += stride)
-    a.flags[u] = (u < u_n && a.usum[u] != 0.0) ? 1u : 0u;
-}
-
-// Thread per run sum: mu_j element = s / ||s_j|| at mptr_new[j] + (its rank
-// among the kept sums of cluster j), so each row stays in term order.
-__global__ void k_write_entries(UpdateArgs a) {
-  const int64_t e_new = a.mptr_new[a.kt];
-  if (e_new > a.cap) {
+// Block per cluster: its mean row, mu_j element = s / ||s_j|| for every
+// nonzero run sum in term order, written at mptr_new[j] + (the sum's rank
+// among the cluster's nonzero sums: a block-wide running count, 256 sums at
+// a time).  Clusters with ||s_j|| = 0 are left to k_copy_kept.
+__global__ void __launch_bounds__(kNormThreads) k_write_rows(UpdateArgs a) {
+  __shared__ int wcount[kNormThreads / 32];
+  if (a.mptr_new[a.kt] > a.cap) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(a.status, (unsigned)STS_CAPACITY);
     return;
   }
-  const int64_t u_n = *a.d_u;
-  const int tb = a.tbits;
-  const uint64_t tmask = (tb >= 64) ? ~0ull : ((1ull << tb) - 1ull);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint64_t tmask = (a.tbits >= 64) ? ~0ull : ((1ull << a.tbits) - 1ull);
   bool neg = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
-    const double s = a.usum[u];
-    if (s == 0.0) continue;
-    const uint64_t key = a.ukey[u];
-    const int64_t j = (int64_t)(key >> tb);
+  for (int64_t j = blockIdx.x; j < a.kt; j += gridDim.x) {
     const double nrm = a.sum_norm[j];
-    if (!(nrm > 0.0)) continue;
-    const int64_t o = a.mptr_new[j] + (int64_t)(a.flags[u] - a.flags[a.uptr[j]]);
+    if (!(nrm > 0.0)) continue;  // uniform over the block
     const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)j)] : 0;
-    a.mterm_new[o] = (int32_t)(key & tmask) + t0;
-    a.mval_new[o] = __ddiv_rn(s, nrm);
-    a.mclu_new[o] = (int32_t)j;
-    neg |= s < 0.0;
+    const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
+    int64_t o = a.mptr_new[j];
+    for (int64_t c0 = u0; c0 < u1; c0 += kNormThreads) {
+      const int64_t u = c0 + threadIdx.x;
+      const double s = u < u1 ? a.usum[u] : 0.0;
+      const bool keep = s != 0.0;
+      const unsigned m = __ballot_sync(IVF_FULL_MASK, keep);
+      if (lane == 0) wcount[warp] = __popc(m);
+      __syncthreads();
+      int before = 0, total = 0;
+      for (int w = 0; w < kNormThreads / 32; ++w) {
+        before += w < warp ? wcount[w] : 0;
+        total += wcount[w];
+      }
+      if (keep) {
+        const int64_t p = o + before + __popc(m & ((1u << lane) - 1u));
+        a.mterm_new[p] = (int32_t)(a.ukey[u] & tmask) + t0;
+        a.mval_new[p] = __ddiv_rn(s, nrm);
+        a.mclu_new[p] = (int32_t)j;
+        neg |= s < 0.0;
+      }
+      o += total;
+      __syncthreads();
+    }
   }
-  if (__any_sync(IVF_FULL_MASK, neg) && (threadIdx.x & 31) == 0) atomicOr(a.means_negative, 1u);
+  if (__any_sync(IVF_FULL_MASK, neg) && lane == 0) atomicOr(a.means_negative, 1u);
 }
 
 // Warp per cluster with no members (or a zero sum) under empty_policy 0:
@@ -277,14 +283,26 @@ __global__ void k_copy_kept(UpdateArgs a) {
 
 // ------------------------------------------------------- A8 inverted file
 
+// Key = term; payload = (local cluster << 32 | the value in the storage
+// type's bits), carried through the sort so the fill reads it in order.
+template <typename WT>
 __global__ void k_ivf_keys(IvfBuildArgs a) {
   const int64_t e_n = a.mptr[a.kt];
   const int64_t n = e_n > a.cap ? 0 : e_n;
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.d_e = n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
-    a.k32a[e] = (uint32_t)a.mterm[e];
-    a.v32a[e] = (uint32_t)e;
+    const int32_t gc = a.mclu[e];
+    const int b = a.n_inst > 1 ? find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc) : 0;
+    const uint32_t local = (uint32_t)(gc - a.inst_clu[b]);
+    const WT w = from_f64<WT>(a.mval[e]);
+    uint32_t bits;
+    if constexpr (sizeof(WT) == 4)
+      bits = __float_as_uint(*reinterpret_cast<const float*>(&w));
+    else
+      bits = (uint32_t)(*reinterpret_cast<const uint16_t*>(&w));
+    a.v32a[e] = (uint32_t)a.mterm[e];
+    a.v64a[e] = ((uint64_t)local << 32) | bits;
   }
 }
 
@@ -296,18 +314,18 @@ __global__ void k_term_ptr(IvfBuildArgs a, const uint32_t* sorted_terms) {
 }
 
 template <typename WT>
-__global__ void k_ivf_fill(IvfBuildArgs a, const uint32_t* perm) {
+__global__ void k_ivf_fill(IvfBuildArgs a, const uint64_t* cv) {
   const int64_t n = *a.d_e;
-  WT* w = static_cast<WT*>(a.w);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) {
-    const uint32_t e = perm[q];
-    const int32_t gc = a.mclu[e];
-    const int b = a.n_inst > 1 ? find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc) : 0;
-    const int32_t local = gc - a.inst_clu[b];
+    const uint64_t x = cv[q];
+    const int32_t local = (int32_t)(x >> 32);
     a.cid32[q] = local;
     a.cid16[q] = (uint16_t)(local & 0xFFFF);
-    w[q] = from_f64<WT>(a.mval[e]);
+    if constexpr (sizeof(WT) == 4)
+      static_cast<uint32_t*>(a.w)[q] = (uint32_t)x;
+    else
+      static_cast<uint16_t*>(a.w)[q] = (uint16_t)x;
   }
 }
 
@@ -507,17 +525,14 @@ __global__ void k_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsig
 // A7 from the run sums of A6 (ukey, usum, *d_u <= u_max): norms, new row
 // lengths, prefix sums, the normalised entries, kept rows of empty clusters.
 cudaError_t launch_means_from_sums(const UpdateArgs& a, int64_t u_max, cudaStream_t s) {
-  const unsigned gE = grid_for(u_max, T256, 16384);
+  (void)u_max;  // the run sums are read per cluster (uptr), not by a flat pass
   const unsigned gK = grid_for(a.kt + 1, T256, 8192);
   k_uptr<<<gK, T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   k_cluster_norm<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
-  k_keep_flags<<<gE, T256, 0, s>>>(a, u_max);
-  IVF_LAUNCH_CHECK();
-  IVF_CU(exclusive_scan_u32(a.flags, a.flags, u_max, a.temp, s));  // flags[u_max] <- total
-  k_write_entries<<<gE, T256, 0, s>>>(a);
+  k_write_rows<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   k_copy_kept<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
@@ -695,23 +710,33 @@ cudaError_t launch_build_zeta(const ZetaArgs& z, cudaStream_t s) {
 
 cudaError_t launch_build_ivf(const IvfBuildArgs& a, cudaStream_t s) {
   const unsigned gE = grid_for(a.cap, T256, 16384);
-  k_ivf_keys<<<gE, T256, 0, s>>>(a);
+  switch (a.storage) {
+    case ST_F16:
+      k_ivf_keys<__half><<<gE, T256, 0, s>>>(a);
+      break;
+    case ST_BF16:
+      k_ivf_keys<__nv_bfloat16><<<gE, T256, 0, s>>>(a);
+      break;
+    default:
+      k_ivf_keys<float><<<gE, T256, 0, s>>>(a);
+      break;
+  }
   IVF_LAUNCH_CHECK();
   bool alt = false;
-  IVF_CU(radix_sort_u32(a.k32a, a.k32b, a.v32a, a.v32b, a.d_e, a.cap, a.tbits, a.temp, s, &alt));
-  const uint32_t* terms = alt ? a.k32b : a.k32a;
-  const uint32_t* perm = alt ? a.v32b : a.v32a;
+  IVF_CU(radix_sort_u32_wide(a.v32a, a.v32b, a.v64a, a.v64b, a.d_e, a.cap, a.tbits, a.temp, s, &alt));
+  const uint32_t* terms = alt ? a.v32b : a.v32a;
+  const uint64_t* cv = alt ? a.v64b : a.v64a;
   k_term_ptr<<<grid_for(a.dt + 1, T256, 16384), T256, 0, s>>>(a, terms);
   IVF_LAUNCH_CHECK();
   switch (a.storage) {
     case ST_F16:
-      k_ivf_fill<__half><<<gE, T256, 0, s>>>(a, perm);
+      k_ivf_fill<__half><<<gE, T256, 0, s>>>(a, cv);
       break;
     case ST_BF16:
-      k_ivf_fill<__nv_bfloat16><<<gE, T256, 0, s>>>(a, perm);
+      k_ivf_fill<__nv_bfloat16><<<gE, T256, 0, s>>>(a, cv);
       break;
     default:
-      k_ivf_fill<float><<<gE, T256, 0, s>>>(a, perm);
+      k_ivf_fill<float><<<gE, T256, 0, s>>>(a, cv);
       break;
   }
   IVF_LAUNCH_CHECK();
