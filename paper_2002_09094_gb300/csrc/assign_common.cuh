@@ -11,14 +11,15 @@
 
 namespace ivfk {
 
+// Push similarity x of cluster xid into (best b of id, second s).  Every
+// caller pushes one thread's clusters in ascending id, so a tie keeps the
+// earlier, lower id and only a strictly larger x takes the best place
+// (branch-free: three selects and a max).
 __device__ __forceinline__ void top2_push(float& b, int& id, float& s, float x, int xid) {
-  if (x > b || (x == b && xid < id)) {
-    s = b;
-    b = x;
-    id = xid;
-  } else if (x > s) {
-    s = x;
-  }
+  const bool gt = x > b;
+  s = gt ? b : fmaxf(s, x);
+  id = gt ? xid : id;
+  b = gt ? x : b;
 }
 
 __device__ __forceinline__ void top2_merge(float& b, int& id, float& s, float b2, int id2, float s2) {
