@@ -341,7 +341,7 @@ def assign_roofline(c, w, storage, timing, info, l2_gbs, schedule):
             "frac": round(achieved / l2_gbs, 4), "traffic": traffic,
             "peak_source": "L2 read bandwidth of a resident set, measured live on this GPU by ivf_probe_l2_read "
                            "(builder-measured; not a driver peak)",
-            "kernel": ("assign step: k_build_xhead + cuBLAS GEMM + k_assign" if info["dense_head_tensor"]
+            "kernel": ("assign step: k_build_xhead + k_tc_head (tcgen05) + k_assign" if info["dense_head_tensor"]
                        else "assign step: k_assign (%s)" % schedule),
             "algorithmic_bytes_per_launch": int(b_assign), "entries_per_launch": int(entries),
             "kernel_ms": round(kern_ms, 4),

@@ -74,7 +74,8 @@ typedef enum { IVF_F32 = 0, IVF_F16 = 1, IVF_BF16 = 2 } ivf_dtype;
 #define IVF_FLAG_SPARSE_ONLY 8u /* autotune only among kernels that read the sparse lists alone */
 #define IVF_FLAG_TENSOR_HEAD 16u /* FP16/BF16 storage: autotune only among dense-head kernels whose
                                     head part is a tensor-core GEMM of the objects' dense head
-                                    values with the dense rows (cuBLAS), batch by batch */
+                                    values with the dense rows (the library's tcgen05 kernel),
+                                    batch by batch */
 #define IVF_FLAG_TILE_MAJOR 32u  /* autotune only among tile-major schedules: one launch per tile of the
                                     cluster range over all objects, (best, id, second) carried in
                                     device memory between launches (tiled shapes, one instance) */
@@ -328,8 +329,8 @@ ivf_status ivf_head_product(int64_t m, int32_t n, int32_t k, const void* a, int6
  * synchronises the stream. */
 ivf_status ivf_probe_l2_read(int64_t bytes, int32_t reps, void* cuda_stream, double* gbs_out);
 
-/* Number of kernels this library has launched in the process so far (its
- * own kernels; the cuBLAS GEMM of the tensor-core head is not counted). */
+/* Number of kernels this library has launched in the process so far (all
+ * of them its own, the tensor-core head product included). */
 int64_t ivf_launch_count(void);
 /* Library version string. */
 const char* ivf_version(void);
@@ -337,9 +338,9 @@ const char* ivf_version(void);
 /* ------------------------------------------------------------------------
  * Batched form: many independent clustering problems of uneven N, K and D
  * in one context.  Every launch (re-score, update) covers all instances at
- * once, and the assignment one launch per class of instances by K (<= 512,
- * <= 1,024, larger), each with its own autotuned kernel; no arithmetic mixes
- * instances.
+ * once, and the assignment one launch per class of instances by K (<= 128,
+ * <= 256, <= 512, <= 1,024, larger), each with its own autotuned kernel; no
+ * arithmetic mixes instances.
  * inst_docs int64[n_inst+1]: object offsets (row_ptr is the concatenation of
  *   the instances' CSR rows, term ids local to the instance);
  * inst_terms int32[n_inst]: D of each instance; inst_k int32[n_inst]: K.

@@ -124,7 +124,7 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
   const WT* __restrict__ wd = static_cast<const WT*>(a.wd);
   const int32_t* __restrict__ head_slot = a.head_slot;
   // (tensor-core head parts exist for 16-bit storage only)
-  const WT* __restrict__ rho_tc = (R > 0 && TC) ? static_cast<const WT*>(a.rho_head) : nullptr;
+  const __half* __restrict__ rho_tc = (R > 0 && TC) ? static_cast<const __half*>(a.rho_head) : nullptr;
   constexpr int RR = R > 0 ? R : 1;
   constexpr int VEC = 16 / (int)sizeof(WT);      // values per 16-byte load of a dense head row
   constexpr int NG = RR >= VEC ? RR / VEC : 1;  // 16-byte groups per lane: clusters VEC*(32g + lane) + k
@@ -385,12 +385,12 @@ __global__ void __maxnreg__((assign_max_regs<WT, R, TC>())) k_assign(const Assig
           }
           if (rho_tc != nullptr) {
             // the head part from the tensor-core GEMM: same lane-to-cluster map
-            const WT* __restrict__ rr = rho_tc + (i - a.obj_base) * a.rho_ld + lo + sbase;
+            const __half* __restrict__ rr = rho_tc + (i - a.obj_base) * a.rho_ld + lo + sbase;
 #pragma unroll
             for (int g = 0; g < NG; ++g) {
               if (g < ng_live) {
                 float e[VEC];
-                unpack16<WT>(__ldg(reinterpret_cast<const uint4*>(rr + VEC * (32 * g + lane))), e);
+                unpack16<__half>(__ldg(reinterpret_cast<const uint4*>(rr + VEC * (32 * g + lane))), e);
 #pragma unroll
                 for (int k = 0; k < VEC; ++k) acc[g * VEC + k] = e[k];
               }

@@ -90,10 +90,14 @@ __device__ __forceinline__ ErrBound err_bound(int m, float nx, int storage, bool
     const float u16 = storage == ST_F16 ? 4.8828125e-04f : 3.90625e-03f;
     const float up = u16 + 2.f * u32;
     c = 2.f * up + up * up;
-    // a tensor-core head part arrives rounded to the storage type: one more
-    // relative u16 on the head products' sum (|H| <= sum of |v u| there)
-    if (tc_head) c += u16;
     sub = storage == ST_F16 ? fm * u32 * (1.f + up) : fm * 1e-37f;
+    // a tensor-core head part arrives rounded to FP16 (for either storage
+    // type): one more relative 2^-11 on the head products' sum
+    // (|H| <= sum of |v u| there) and half the FP16 subnormal spacing
+    if (tc_head) {
+      c += 4.8828125e-04f;
+      sub += 2.9802322e-08f;
+    }
   }
   ErrBound b;
   if (nonneg) {

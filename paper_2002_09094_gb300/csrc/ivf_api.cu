@@ -37,7 +37,7 @@ struct DevCounters {
   unsigned long long work;
   unsigned long long entries;
   unsigned long long n_rescored;
-  unsigned long long work_cls[4];   // work counters of the per-class launches (batched contexts)
+  unsigned long long work_cls[8];   // work counters of the per-class launches (batched contexts)
   unsigned long long zero_sim;      // objects that met no posting entry in the last assignment
   unsigned long long work_re;       // work counter of the object-major pass over near-ties
   unsigned long long entries_re;    // entries of that pass (already counted by the sweep)
@@ -218,7 +218,7 @@ struct ivf_ctx {
   int64_t scratch_len = 0;
   // launch shape (of the class holding the largest K in a batched context)
   Shape shape;
-  // Batched contexts: instances grouped by K (<= 512, <= 1,024, larger), one
+  // Batched contexts: instances grouped by K (<= 128, <= 256, <= 512, <= 1,024, larger), one
   // assignment launch per class, each with its own kernel; the last class
   // holds the largest K and uses `shape` (the only one that may be tiled).
   struct ClassPlan {
@@ -495,8 +495,10 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   c->cand_slots = std::min<int64_t>(N, int64_t(1) << 20);
   // batched: classes of instances by K (see ClassPlan); autotuned contexts only
   if (n_inst > 1 && cfg->k_tile == 0 && cfg->warps_per_block == 0) {
-    const int32_t bounds[3] = {512, 1024, INT32_MAX};
-    for (int32_t lo = 0, q = 0; q < 3; lo = bounds[q], ++q) {
+    // classes by K: each gets its own kernel (tiny K favours the sparse
+    // kernel, larger K the dense-head register tiles)
+    const int32_t bounds[5] = {128, 256, 512, 1024, INT32_MAX};
+    for (int32_t lo = 0, q = 0; q < 5; lo = bounds[q], ++q) {
       ivf_ctx::ClassPlan p;
       std::vector<int64_t> prefix(1, 0);
       for (int32_t b = 0; b < n_inst; ++b)
@@ -1039,6 +1041,7 @@ ivf_status enqueue_tc_gemm(ivf_ctx* c, int64_t b0, int64_t nb) {
   h.d = c->rho_h;
   h.ldd = c->kpad;
   h.bf16 = c->cfg.storage == IVF_BF16;
+  h.out_bf16 = false;  // FP16 product: 2^-11 rounding for either storage type
   h.chunk_nz = c->chunk_nz;
   h.status = &c->dc->status;
   h.num_sms = c->num_sms;

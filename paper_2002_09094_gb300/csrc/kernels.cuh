@@ -74,9 +74,10 @@ struct AssignArgs {
   int32_t head_sub = 1;         // head sub-tiles of 32 * head_r clusters per shared-memory tile
   // Tensor-core head (16-bit storage): the head part of rho for objects
   // obj_base + o was computed beforehand by a GEMM of the objects' dense head
-  // values with the dense rows (FP32 accumulation, stored in the storage
-  // type), rho_head[o * rho_ld + cluster]; the kernel reads it instead of
-  // walking the rows.
+  // values with the dense rows (FP32 accumulation, stored as FP16 whatever
+  // the storage type: 2^-11 relative rounding, |rho| <= ||x|| far below the
+  // FP16 range), rho_head[o * rho_ld + cluster]; the kernel reads it instead
+  // of walking the rows.
   const void* rho_head;
   int64_t rho_ld;
   int64_t obj_base;
@@ -319,9 +320,10 @@ cudaError_t launch_build_xhead(int64_t i0, int64_t nb, const int64_t* row_ptr, c
                                uint8_t* chunk_nz, cudaStream_t s);
 
 // Tensor-core head product (tc_head.cu): d[i][c] = sum_s a[i][s] * b[c][s]
-// for i < m, c < n, s < k; a, b, d 16-bit (bf16 or fp16), row-major with
-// leading dimensions lda, ldb, ldd (elements, multiples of 8; pointers
-// 16-byte aligned), FP32 accumulation, d rounded to the 16-bit type.
+// for i < m, c < n, s < k; a, b 16-bit (both bf16 or both fp16), d 16-bit
+// (bf16 or fp16), row-major with leading dimensions lda, ldb, ldd (elements,
+// multiples of 8; pointers 16-byte aligned), FP32 accumulation, d rounded to
+// its 16-bit type.
 // n a multiple of 256, k a multiple of 64.  chunk_nz (or null): per
 // 128-row block of a and 64-column chunk, 0 when that chunk of a is zero
 // (skipped).  A bounded wait that runs out sets STS_TIMEOUT in *status.
@@ -334,7 +336,8 @@ struct TcHeadArgs {
   int64_t ldb;
   void* d;
   int64_t ldd;
-  bool bf16;
+  bool bf16;      // a and b are bf16 (else fp16)
+  bool out_bf16;  // d is bf16 (else fp16)
   const uint8_t* chunk_nz;
   unsigned* status;
   int num_sms;

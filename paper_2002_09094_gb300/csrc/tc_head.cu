@@ -18,8 +18,8 @@
 //     flop of a 128-object tile -- into two FP32 accumulators in TMEM (512
 //     columns);
 //   * eight epilogue warps read the accumulators with tcgen05.ld and store
-//     them in the storage type (the assignment kernel adds the sparse tail
-//     and takes the argmax);
+//     them as FP16 for the assignment (which adds the sparse tail and takes
+//     the argmax), or in the operands' type for ivf_head_product;
 //   * a K-chunk of 64 head slots that is zero for all 256 objects of a tile
 //     (flags from the kernel that builds x_h, per 128 objects) is neither
 //     loaded nor multiplied;
@@ -198,6 +198,8 @@ __device__ __forceinline__ uint32_t pack2(uint32_t lo, uint32_t hi) {
   }
 }
 
+// BF16: the output type (the operand type is in the instruction descriptor
+// and the tensor maps).
 template <bool BF16>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_head(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, const TcArgs a) {
@@ -429,12 +431,12 @@ cudaError_t launch_tc_head(const TcHeadArgs& h, cudaStream_t s) {
   a.k = h.k;
   a.d = static_cast<uint16_t*>(h.d);
   a.ldd = h.ldd;
-  a.idesc = make_idesc(h.bf16);
+  a.idesc = make_idesc(h.bf16);  // the operand type; the output type is the kernel's template argument
   a.chunk_nz = h.chunk_nz;
   a.status = h.status;
   const int64_t tiles = ((h.m + BM - 1) / BM) * (h.n / BN);
   const int grid = (int)(tiles < h.num_sms ? tiles : h.num_sms);
-  if (h.bf16)
+  if (h.out_bf16)
     k_tc_head<true><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
   else
     k_tc_head<false><<<grid, THREADS, SMEM_BYTES, s>>>(ma, mb, a);
@@ -472,6 +474,7 @@ extern "C" ivf_status ivf_head_product(int64_t m, int32_t n, int32_t k, const vo
   h.d = d;
   h.ldd = ldd;
   h.bf16 = storage == IVF_BF16;
+  h.out_bf16 = h.bf16;
   h.chunk_nz = nullptr;
   h.status = st;
   h.num_sms = sms;

@@ -138,12 +138,18 @@ def test_batched_equals_single_instances():
 
 
 @pytest.mark.parametrize("kernel,seed,n_inst", [("sparse", 77, 4), ("dense_head", 77, 4), ("auto", 85, 5),
-                                                ("dense_head", 88, 5)])
+                                                ("dense_head", 88, 5), ("auto", 98, 32)])
 def test_batched_lockstep_against_oracle(kernel, seed, n_inst):
     """Seed 77: K in two of the classes the batched assignment launches
-    separately (<= 1,024 and larger); seeds 85 and 88: all three classes."""
-    ws = dg.batched_workloads(n_instances=n_inst, n_range=(800, 2000), k_range=(8, 1600 if n_inst == 5 else 1500),
+    separately (<= 1,024 and larger); seeds 85 and 88: three classes; seed 98:
+    32 instances with K in all five classes (<= 128, <= 256, <= 512,
+    <= 1,024, larger)."""
+    ws = dg.batched_workloads(n_instances=n_inst, n_range=(800, 2000), k_range=(8, 1500 if n_inst == 4 else 1600),
                               d_range=(2000, 5000), nnz_range=(15.0, 50.0), iterations=3, seed=seed)
+    if n_inst == 32:
+        ks = [w.k for w in ws]
+        assert all(any(lo < k <= hi for k in ks) for lo, hi in [(0, 128), (128, 256), (256, 512), (512, 1024),
+                                                                (1024, 1 << 30)])
     cs = [dg.make_corpus(w.corpus) for w in ws]
     ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
     inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
