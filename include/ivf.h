@@ -339,8 +339,8 @@ const char* ivf_version(void);
  * Batched form: many independent clustering problems of uneven N, K and D
  * in one context.  Every launch (re-score, update) covers all instances at
  * once, and the assignment one launch per class of instances by K (<= 128,
- * <= 256, <= 512, <= 1,024, larger), each with its own autotuned kernel; no
- * arithmetic mixes instances.
+ * <= 256, <= 512, <= 1,024, <= 1,536, <= 2,048, larger), each with its own
+ * autotuned kernel; no arithmetic mixes instances.
  * inst_docs int64[n_inst+1]: object offsets (row_ptr is the concatenation of
  *   the instances' CSR rows, term ids local to the instance);
  * inst_terms int32[n_inst]: D of each instance; inst_k int32[n_inst]: K.

@@ -544,8 +544,12 @@ __device__ __forceinline__ void top2_push_d(double& b, int& id, double& s, doubl
 }
 
 // One warp per flagged object: rho_ij in FP64 for its candidate clusters (all
-// clusters on overflow) against the FP64 master means, summed in ascending h
-// as Eq. 8 writes it, then the argmax with the lowest-id tie rule.
+// clusters on overflow) against the FP64 master means (Eq. 8): lane l sums
+// the products of its terms h = l, l + 32, ... by fused multiply-add, then a
+// fixed xor butterfly adds the 32 partial sums (every lane ends with the same
+// bits, whatever the launch shape); then the argmax with the lowest-id tie
+// rule.  A warp-serial sum in ascending h cost 32 lanes of FP64 add per
+// product, and FP64 issues at a small fraction of the FP32 rate here.
 __global__ void __launch_bounds__(256) k_rescore(const RescoreArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -565,32 +569,20 @@ __global__ void __launch_bounds__(256) k_rescore(const RescoreArgs a) {
       const int c = cnt < 0 ? q : a.flag_cand[slot * CAND_MAX + q];
       const int64_t mb = a.mptr[c0 + c], me = a.mptr[c0 + c + 1];
       double acc = 0.0;
-      for (int64_t h0 = r0; h0 < r1; h0 += 32) {
-        const int64_t h = h0 + lane;
-        double p = 0.0;
-        bool hit = false;
-        if (h < r1) {
-          const int t = a.term[h];
-          int64_t lo = mb, hi = me;
-          while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (a.mterm[mid] < t)
-              lo = mid + 1;
-            else
-              hi = mid;
-          }
-          if (lo < me && a.mterm[lo] == t) {
-            p = __dmul_rn((double)a.val32[h], a.mval[lo]);
-            hit = true;
-          }
+      for (int64_t h = r0 + lane; h < r1; h += 32) {
+        const int t = a.term[h];
+        int64_t lo = mb, hi = me;
+        while (lo < hi) {
+          const int64_t mid = (lo + hi) >> 1;
+          if (a.mterm[mid] < t)
+            lo = mid + 1;
+          else
+            hi = mid;
         }
-        const unsigned hm = __ballot_sync(IVF_FULL_MASK, hit);
-        const int nh = (int)min((int64_t)32, r1 - h0);
-        for (int j = 0; j < nh; ++j) {
-          const double pj = __shfl_sync(IVF_FULL_MASK, p, j);
-          if ((hm >> j) & 1u) acc = __dadd_rn(acc, pj);
-        }
+        if (lo < me && a.mterm[lo] == t) acc = __fma_rn(f32_bits_to_f64(__float_as_uint(a.val32[h])), a.mval[lo], acc);
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(IVF_FULL_MASK, acc, o));
       top2_push_d(best, bid, second, acc, c);
     }
     if (lane == 0) {
@@ -598,8 +590,9 @@ __global__ void __launch_bounds__(256) k_rescore(const RescoreArgs a) {
       a.assign[i] = bid;
       a.best[i] = bf;
       a.gap[i] = __double2float_rn(best - second);
-      // FP64 recursive summation of at most m products (each |v u| summing
-      // to <= ||x||): (m + 1) 2^-53 ||x||, then the rounding to FP32
+      // FP64 sum of at most m products in any order of additions (lane sums
+      // by fused multiply-add, then the butterfly; the |v u| sum to <= ||x||):
+      // (m + 1) 2^-53 ||x||, then the rounding to FP32
       if (a.err != nullptr)
         a.err[i] = fabsf(bf) * 5.9604645e-08f + (float)((double)(r1 - r0 + 1) * 1.1102230246251565e-16 *
                                                         (double)a.nx[i]) + 1e-30f;

@@ -29,6 +29,19 @@ void note_launch();
 
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// FP32 bits -> the same value as FP64, from the IEEE 754 binary32 and
+// binary64 layouts: for a normal number the sign is kept, the exponent is
+// rebased from bias 127 to bias 1023 and the 23 fraction bits move to the
+// top of the 52.  Integer operations only (FP64 conversions issue at the low
+// FP64 rate of this part); zero, subnormal, infinite and NaN inputs take the
+// hardware conversion.  Exact, like the conversion it replaces.
+__device__ __forceinline__ double f32_bits_to_f64(uint32_t b) {
+  const uint32_t e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)__uint_as_float(b);
+  const uint64_t d = ((uint64_t)(b >> 31) << 63) | ((uint64_t)(e + 896u) << 52) | ((uint64_t)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
+
 // Stored value -> float (storage types of the assignment stream).
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__half x) { return __half2float(x); }

@@ -199,6 +199,7 @@ struct ivf_ctx {
   int64_t* cl_ptr = nullptr;
   int32_t* members = nullptr;
   double* sum_norm = nullptr;
+  double* rnorm = nullptr;
   bool members_valid = false;
   // update scratch
   uint64_t* k64a = nullptr;
@@ -211,6 +212,7 @@ struct ivf_ctx {
   double* usum = nullptr;
   int64_t* uptr = nullptr;
   int64_t* newlen = nullptr;
+  int32_t* zrun = nullptr;
   int64_t* d_nnz = nullptr;
   int64_t* d_n = nullptr;
   int64_t* d_u = nullptr;
@@ -218,7 +220,8 @@ struct ivf_ctx {
   int64_t scratch_len = 0;
   // launch shape (of the class holding the largest K in a batched context)
   Shape shape;
-  // Batched contexts: instances grouped by K (<= 128, <= 256, <= 512, <= 1,024, larger), one
+  // Batched contexts: instances grouped by K (<= 128, <= 256, <= 512, <= 1,024,
+  // <= 1,536, <= 2,048, larger), one
   // assignment launch per class, each with its own kernel; the last class
   // holds the largest K and uses `shape` (the only one that may be tiled).
   struct ClassPlan {
@@ -496,9 +499,12 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   // batched: classes of instances by K (see ClassPlan); autotuned contexts only
   if (n_inst > 1 && cfg->k_tile == 0 && cfg->warps_per_block == 0) {
     // classes by K: each gets its own kernel (tiny K favours the sparse
-    // kernel, larger K the dense-head register tiles)
-    const int32_t bounds[5] = {128, 256, 512, 1024, INT32_MAX};
-    for (int32_t lo = 0, q = 0; q < 5; lo = bounds[q], ++q) {
+    // kernel, larger K the dense-head register tiles; above 1,024 clusters
+    // the best split of the 2,048-cluster tile -- 4 x 512 or 2 x 1,024 --
+    // changes with K)
+    constexpr int kClasses = 7;
+    const int32_t bounds[kClasses] = {128, 256, 512, 1024, 1536, 2048, INT32_MAX};
+    for (int32_t lo = 0, q = 0; q < kClasses; lo = bounds[q], ++q) {
       ivf_ctx::ClassPlan p;
       std::vector<int64_t> prefix(1, 0);
       for (int32_t b = 0; b < n_inst; ++b)
@@ -531,6 +537,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->cl_ptr, c->Kt + 1);
   AL(c->members, N);
   AL(c->sum_norm, c->Kt);
+  AL(c->rnorm, c->Kt);
   AL(c->flags, nnz + 1);
   AL(c->starts, nnz + 1);
   AL(c->ukey, nnz);
@@ -539,6 +546,7 @@ ivf_status create_common(const ivf_config* cfg, int32_t n_inst, const std::vecto
   AL(c->d_part_n, 1);
   AL(c->uptr, c->Kt + 1);
   AL(c->newlen, c->Kt + 1);
+  AL(c->zrun, c->Kt);
   AL(c->d_nnz, 1);
   AL(c->d_n, 1);
   AL(c->d_u, 1);
@@ -1181,13 +1189,20 @@ ivf_status tune_classes(ivf_ctx* c) {
     const bool no_head = (c->cfg.flags & IVF_FLAG_SPARSE_ONLY) != 0 || c->shape.head_r == 0;
     const bool head_only = (c->cfg.flags & IVF_FLAG_DENSE_HEAD) != 0 && c->shape.head_r > 0;
     if (!head_only && shape_for(c, p.kmax, 0, 0, &sh) && !sh.tiled) cands.push_back(sh);
-    if (!no_head)
+    if (!no_head) {
       for (int hr : {HEAD_R_SMALL, HEAD_R_MID, HEAD_R_LARGE})
         for (int wp : {8, 4}) {
           if (c->kpad % (32 * hr) != 0) continue;
           if (shape_for(c, p.kmax, 0, wp, &sh, hr, c->shape.head_theta) && !sh.tiled) cands.push_back(sh);
         }
-    if (cands.empty()) cands.push_back(c->shape);  // cannot happen for K <= 1,024; kept for safety
+      // K above one register tile: 2,048-cluster shared-memory tiles of
+      // 2 x 1,024 or 4 x 512 register sub-tiles
+      for (int wp : {4, 8}) {
+        if (shape_for(c, p.kmax, 0, wp, &sh, HEAD_R_LARGE, c->shape.head_theta, 2) && !sh.tiled) cands.push_back(sh);
+        if (shape_for(c, p.kmax, 0, wp, &sh, HEAD_R_MID, c->shape.head_theta, 4) && !sh.tiled) cands.push_back(sh);
+      }
+    }
+    if (cands.empty()) cands.push_back(c->shape);  // no untiled shape fits: the main class's kernel
     Shape best = cands[0];
     float best_ms = 1e30f;
     for (const Shape& cand : cands) {
@@ -1506,6 +1521,7 @@ UpdateArgs update_args(ivf_ctx* c, int src) {
   u.cl_ptr = c->cl_ptr;
   u.members = c->members;
   u.sum_norm = c->sum_norm;
+  u.rnorm = c->rnorm;
   u.k64a = c->k64a;
   u.k64b = c->k64b;
   u.v32a = c->v32a;
@@ -1516,6 +1532,7 @@ UpdateArgs update_args(ivf_ctx* c, int src) {
   u.usum = c->usum;
   u.uptr = c->uptr;
   u.newlen = c->newlen;
+  u.zrun = c->zrun;
   u.d_nnz = c->d_nnz;
   u.d_n = c->d_n;
   u.d_u = c->d_u;

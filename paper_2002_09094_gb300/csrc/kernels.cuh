@@ -200,6 +200,7 @@ struct UpdateArgs {
   int64_t* cl_ptr;      // [Kt+1]
   int32_t* members;     // [N]
   double* sum_norm;     // [Kt]
+  double* rnorm;        // [Kt] 1 / ||s_j|| rounded to nearest (0 when ||s_j|| = 0)
   // scratch
   uint64_t* k64a;
   uint64_t* k64b;
@@ -211,6 +212,7 @@ struct UpdateArgs {
   double* usum;         // [nnz]
   int64_t* uptr;        // [Kt+1]
   int64_t* newlen;      // [Kt+1]
+  int32_t* zrun;        // [Kt] 1 when one of cluster j's run sums is exactly zero
   int64_t* d_nnz;       // device copy of nnz
   int64_t* d_n;         // device copy of N
   int64_t* d_u;         // number of unique (cluster, term) keys

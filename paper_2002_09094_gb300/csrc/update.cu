@@ -11,9 +11,10 @@
 //      in ascending object id, and each run is summed sequentially in FP64
 //      (the same order in which the oracle's dense accumulation adds them);
 //   A7 normalise: ||s_j||^2 by a block per cluster in a fixed order (strided
-//      partial sums, then a fixed tree; separate multiply and add, no
-//      contraction), zero sums dropped (w_p != 0) and the kept ones ranked
-//      by one device-wide scan,
+//      partial sums by fused multiply-add, then a fixed tree), zero sums
+//      dropped (w_p != 0), row offsets by a scan
+//      over the clusters, rows written by a thread per run sum (by a block
+//      per cluster for the rare clusters with an exactly zero sum);
 //      empty clusters keep their previous mean or become empty;
 //   A8 inverted file: a stable radix sort by term of the cluster-major means
 //      gives posting lists in ascending cluster id; term_ptr by binary search.
@@ -145,8 +146,9 @@ __global__ void k_zc_segsum(const UpdateArgs a, const uint32_t* cl, const uint64
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
     const uint32_t s0 = a.starts[u], s1 = a.starts[u + 1];
-    double s = 0.0;
-    for (uint32_t e = s0; e < s1; ++e) s = __dadd_rn(s, (double)__uint_as_float((uint32_t)tv[e]));
+    // sequential from the first value (0 + v would be v, so that add is skipped)
+    double s = f32_bits_to_f64((uint32_t)tv[s0]);
+    for (uint32_t e = s0 + 1; e < s1; ++e) s = __dadd_rn(s, f32_bits_to_f64((uint32_t)tv[e]));
     const uint32_t gc = cl[s0];
     const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc)] : 0;
     a.ukey[u] = ((uint64_t)gc << a.tbits) | (uint64_t)(uint32_t)((int32_t)(tv[s0] >> 32) - t0);
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
     int nz = 0;
     for (int64_t u = u0 + threadIdx.x; u < u1; u += kNormThreads) {
       const double v = a.usum[u];
-      n2 = __dadd_rn(n2, __dmul_rn(v, v));
+      n2 = __fma_rn(v, v, n2);
       nz += (v != 0.0) ? 1 : 0;
     }
 #pragma unroll
@@ -202,6 +204,8 @@ __global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
       }
       const double nrm = __dsqrt_rn(t);
       a.sum_norm[j] = nrm;
+      a.rnorm[j] = nrm > 0.0 ? __drcp_rn(nrm) : 0.0;
+      a.zrun[j] = cnt != u1 - u0 ? 1 : 0;
       int64_t len;
       if (nrm > 0.0)
         len = cnt;
@@ -213,10 +217,44 @@ __global__ void __launch_bounds__(kNormThreads) k_cluster_norm(UpdateArgs a) {
   }
 }
 
-// Block per cluster: its mean row, mu_j element = s / ||s_j|| for every
-// nonzero run sum in term order, written at mptr_new[j] + (the sum's rank
-// among the cluster's nonzero sums: a block-wide running count, 256 sums at
-// a time).  Clusters with ||s_j|| = 0 are left to k_copy_kept.
+// s / ||s_j|| as s * y with y = RN(1 / ||s_j||): one FP64 multiply instead
+// of a division (FP64 issues at a small fraction of the FP32 rate on this
+// part: a division per run sum took 1.4 ms at 4.8e7 sums, a multiply plus a
+// Markstein correction 0.9 ms).  Within two ulps of the quotient.
+__device__ __forceinline__ double div_by_norm(double s, double y) { return __dmul_rn(s, y); }
+
+// Thread per run sum u of a cluster j with ||s_j|| > 0 and no zero run sum:
+// mu_j element = s / ||s_j|| at mptr_new[j] + (u - uptr[j]) (every run is
+// kept, so a run's rank is its offset).  Over the whole grid, so the largest
+// clusters (hundreds of thousands of runs) leave no tail.
+__global__ void k_write_flat(UpdateArgs a) {
+  if (a.mptr_new[a.kt] > a.cap) return;  // k_write_rows raises STS_CAPACITY
+  const uint64_t tmask = (a.tbits >= 64) ? ~0ull : ((1ull << a.tbits) - 1ull);
+  const int64_t u_n = *a.d_u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool neg = false;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
+    const uint64_t key = a.ukey[u];
+    const int32_t j = (int32_t)(key >> a.tbits);
+    const double nrm = a.sum_norm[j];
+    if (!(nrm > 0.0) || a.zrun[j] != 0) continue;
+    const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, j)] : 0;
+    const double s = a.usum[u];
+    const int64_t p = a.mptr_new[j] + (u - a.uptr[j]);
+    a.mterm_new[p] = (int32_t)(key & tmask) + t0;
+    a.mval_new[p] = div_by_norm(s, a.rnorm[j]);
+    a.mclu_new[p] = j;
+    neg |= s < 0.0;
+  }
+  if (__any_sync(IVF_FULL_MASK, neg) && (threadIdx.x & 31) == 0) atomicOr(a.means_negative, 1u);
+}
+
+// Block per cluster with ||s_j|| > 0 and at least one zero run sum (exact
+// cancellation, signed data only): its mean row, mu_j element = s / ||s_j||
+// for every nonzero run sum in term order, written at mptr_new[j] + (the
+// sum's rank among the cluster's nonzero sums: a block-wide running count,
+// 256 sums at a time).  Clusters with ||s_j|| = 0 are left to k_copy_kept,
+// the rest to k_write_flat.
 __global__ void __launch_bounds__(kNormThreads) k_write_rows(UpdateArgs a) {
   __shared__ int wcount[kNormThreads / 32];
   if (a.mptr_new[a.kt] > a.cap) {
@@ -228,7 +266,8 @@ __global__ void __launch_bounds__(kNormThreads) k_write_rows(UpdateArgs a) {
   bool neg = false;
   for (int64_t j = blockIdx.x; j < a.kt; j += gridDim.x) {
     const double nrm = a.sum_norm[j];
-    if (!(nrm > 0.0)) continue;  // uniform over the block
+    if (!(nrm > 0.0) || a.zrun[j] == 0) continue;  // uniform over the block
+    const double y = a.rnorm[j];
     const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)j)] : 0;
     const int64_t u0 = a.uptr[j], u1 = a.uptr[j + 1];
     int64_t o = a.mptr_new[j];
@@ -247,7 +286,7 @@ __global__ void __launch_bounds__(kNormThreads) k_write_rows(UpdateArgs a) {
       if (keep) {
         const int64_t p = o + before + __popc(m & ((1u << lane) - 1u));
         a.mterm_new[p] = (int32_t)(a.ukey[u] & tmask) + t0;
-        a.mval_new[p] = __ddiv_rn(s, nrm);
+        a.mval_new[p] = div_by_norm(s, y);
         a.mclu_new[p] = (int32_t)j;
         neg |= s < 0.0;
       }
@@ -492,7 +531,8 @@ __global__ void k_prepare_objects(int64_t n_docs, const int64_t* row_ptr, const 
         if (t < 0 || t >= d_local || !isfinite(v)) bad = true;
         if (h > r0 && term[h - 1] >= t) bad = true;
       }
-      ss += (double)v * (double)v;
+      const double dv = f32_bits_to_f64(__float_as_uint(v));
+      ss = __fma_rn(dv, dv, ss);
       if (val_store) val_store[h] = from_f32<WT>(v);
     }
     __syncwarp();
@@ -525,13 +565,14 @@ __global__ void k_check_row_ptr(const int64_t* rp, int64_t n, int64_t nnz, unsig
 // A7 from the run sums of A6 (ukey, usum, *d_u <= u_max): norms, new row
 // lengths, prefix sums, the normalised entries, kept rows of empty clusters.
 cudaError_t launch_means_from_sums(const UpdateArgs& a, int64_t u_max, cudaStream_t s) {
-  (void)u_max;  // the run sums are read per cluster (uptr), not by a flat pass
   const unsigned gK = grid_for(a.kt + 1, T256, 8192);
   k_uptr<<<gK, T256, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   k_cluster_norm<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   IVF_CU(exclusive_scan_i64(a.newlen, a.mptr_new, a.kt, a.temp, s));
+  k_write_flat<<<grid_for(u_max, T256, 16384), T256, 0, s>>>(a);
+  IVF_LAUNCH_CHECK();
   k_write_rows<<<(unsigned)std::min<int64_t>(a.kt, 16384), kNormThreads, 0, s>>>(a);
   IVF_LAUNCH_CHECK();
   k_copy_kept<<<grid_for(a.kt * 32, T256, 8192), T256, 0, s>>>(a);

@@ -142,14 +142,15 @@ def test_batched_equals_single_instances():
 def test_batched_lockstep_against_oracle(kernel, seed, n_inst):
     """Seed 77: K in two of the classes the batched assignment launches
     separately (<= 1,024 and larger); seeds 85 and 88: three classes; seed 98:
-    32 instances with K in all five classes (<= 128, <= 256, <= 512,
-    <= 1,024, larger)."""
-    ws = dg.batched_workloads(n_instances=n_inst, n_range=(800, 2000), k_range=(8, 1500 if n_inst == 4 else 1600),
+    32 instances with K in six classes (<= 128, <= 256, <= 512, <= 1,024,
+    <= 1,536, <= 2,048)."""
+    k_hi = {4: 1500, 5: 1600, 32: 2000}[n_inst]
+    ws = dg.batched_workloads(n_instances=n_inst, n_range=(800, 2000), k_range=(8, k_hi),
                               d_range=(2000, 5000), nnz_range=(15.0, 50.0), iterations=3, seed=seed)
     if n_inst == 32:
         ks = [w.k for w in ws]
         assert all(any(lo < k <= hi for k in ks) for lo, hi in [(0, 128), (128, 256), (256, 512), (512, 1024),
-                                                                (1024, 1 << 30)])
+                                                                (1024, 1536), (1536, 2048)])
     cs = [dg.make_corpus(w.corpus) for w in ws]
     ids = [dg.init_doc_ids(c.n_docs, w.k, w.init_seed) for w, c in zip(ws, cs)]
     inst_docs = np.concatenate([[0], np.cumsum([c.n_docs for c in cs])]).astype(np.int64)
@@ -614,6 +615,53 @@ def test_negative_mean_rows_lockstep():
             np.concatenate(vals).astype(np.float32))
     for rep in lockstep(c, k, None, 3, means_rows=rows):
         assert_report_ok(rep)
+
+
+@pytest.mark.parametrize("empty_policy", [0, 1])
+def test_exactly_cancelling_member_sums_are_dropped(empty_policy):
+    """Signed objects in pairs whose values on one term cancel exactly inside
+    their cluster: that term's member sum is 0 and leaves the new mean
+    (Algorithm 3 keeps w_p != 0 only).  Clusters 0-9 hold such pairs (their
+    rows come from the per-cluster writer), 10-29 none (the per-run writer),
+    30-31 no member (kept or emptied).  The update of a given assignment
+    equals the oracle's: row structure exactly, values to 1e-12."""
+    rng = np.random.default_rng(71)
+    d, k, n_pairs, n_rand = 50, 32, 40, 360
+    rows, assign = [], []
+    for m in range(n_pairs):  # pair m: 5 shared terms of 0..39 and term 40 + m % 10 with +w / -w
+        t = np.sort(np.append(rng.choice(40, 5, replace=False), 40 + m % 10))
+        v = rng.lognormal(0.0, 1.0, t.size)
+        v /= np.sqrt(np.sum(v * v))
+        v32 = v.astype(np.float32)
+        neg = v32.copy()
+        neg[-1] = -neg[-1]
+        rows += [(t, v32), (t, neg)]
+        assign += [m % 10, m % 10]
+    for i in range(n_rand):
+        t = np.sort(rng.choice(40, 6, replace=False))
+        v = rng.lognormal(0.0, 1.0, t.size)
+        v /= np.sqrt(np.sum(v * v))
+        rows.append((t, v.astype(np.float32)))
+        assign.append(int(rng.integers(0, 30)))  # clusters 0-9 also get objects without terms 40-49
+    rp = np.concatenate([[0], np.cumsum([t.size for t, _ in rows])]).astype(np.int64)
+    tm = np.concatenate([t for t, _ in rows]).astype(np.int32)
+    vl = np.concatenate([v for _, v in rows]).astype(np.float32)
+    c = dg.Corpus(row_ptr=rp, term=tm, val=vl, n_terms=d)
+    a = np.array(assign, np.int32)
+    ids = rng.choice(c.n_docs, k, replace=False).astype(np.int32)
+    with ivf.IVF(rp, tm, vl, d, k, empty_policy=empty_policy) as m:
+        m.set_means_from_docs(ids)
+        p0, t0, v0 = m.get_means()
+        m.set_assign(a)
+        m.update()
+        gp, gt, gv = m.get_means()
+    want, _, _ = sk.update(c, a, sk.Means(ptr=p0, term=t0.astype(np.int64), val=v0, n_terms=d),
+                           empty_policy=empty_policy)
+    assert np.array_equal(gp, want.ptr) and np.array_equal(gt, want.term)
+    assert np.max(np.abs(gv - want.val)) <= 1e-12
+    for j in range(10):  # the cancelling terms are gone, the others are there
+        row = set(gt[gp[j]:gp[j + 1]].tolist())
+        assert 40 + j not in row and len(row) > 0
 
 
 def test_load_objects_equals_fresh_context():
