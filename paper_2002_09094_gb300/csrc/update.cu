@@ -147,8 +147,8 @@ __global__ void k_zc_segsum(const UpdateArgs a, const uint32_t* cl, const uint64
   for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < u_n; u += stride) {
     const uint32_t s0 = a.starts[u], s1 = a.starts[u + 1];
     // sequential from the first value (0 + v would be v, so that add is skipped)
-    double s = f32_bits_to_f64((uint32_t)tv[s0]);
-    for (uint32_t e = s0 + 1; e < s1; ++e) s = __dadd_rn(s, f32_bits_to_f64((uint32_t)tv[e]));
+    double s = (double)__uint_as_float((uint32_t)tv[s0]);
+    for (uint32_t e = s0 + 1; e < s1; ++e) s = __dadd_rn(s, (double)__uint_as_float((uint32_t)tv[e]));
     const uint32_t gc = cl[s0];
     const int32_t t0 = a.n_inst > 1 ? (int32_t)a.inst_toff[find_inst<int32_t>(a.inst_clu, a.n_inst, (int32_t)gc)] : 0;
     a.ukey[u] = ((uint64_t)gc << a.tbits) | (uint64_t)(uint32_t)((int32_t)(tv[s0] >> 32) - t0);
