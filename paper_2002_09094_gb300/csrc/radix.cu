@@ -107,6 +107,35 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const T* in, T* out
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = part[gridDim.x];
 }
 
+// The exclusive scan of 0/1 run-head flags, turned at once into the run
+// starts: the r-th set flag's position goes to starts[r] (so the scanned
+// flags are never written), starts[U] = n and *d_u = U, the number of runs.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_heads(const uint32_t* in, int64_t n, const uint32_t* part,
+                                                             uint32_t* starts, int64_t* d_u) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_ITEMS;
+  uint32_t v[SCAN_ITEMS];
+  uint32_t tsum = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    const int64_t idx = base + i;
+    v[i] = idx < n ? in[idx] : 0u;
+    tsum += v[i];
+  }
+  uint32_t tot;
+  const uint32_t incl = block_inclusive(tsum, &tot);
+  uint32_t run = part[blockIdx.x] + incl - tsum;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; ++i) {
+    if (v[i] != 0u) starts[run] = (uint32_t)(base + i);
+    run += v[i];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const uint32_t u = part[gridDim.x];
+    starts[u] = (uint32_t)n;
+    *d_u = (int64_t)u;
+  }
+}
+
 template <typename T>
 cudaError_t scan_impl(const T* in, T* out, int64_t n, void* temp, cudaStream_t s) {
   int64_t nb = ceil_div(n, SCAN_CHUNK);
@@ -310,6 +339,20 @@ cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, voi
 
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s) {
   return scan_impl<int64_t>(in, out, n, temp, s);
+}
+
+cudaError_t heads_to_starts(const uint32_t* flags, int64_t n, uint32_t* starts, int64_t* d_u, void* temp,
+                            cudaStream_t s) {
+  int64_t nb = ceil_div(n, SCAN_CHUNK);
+  if (nb < 1) nb = 1;
+  uint32_t* part = static_cast<uint32_t*>(temp);
+  k_scan_reduce<uint32_t><<<(unsigned)nb, SCAN_THREADS, 0, s>>>(flags, n, part);
+  IVF_LAUNCH_CHECK();
+  k_scan_partials<uint32_t><<<1, 1024, 0, s>>>(part, nb);
+  IVF_LAUNCH_CHECK();
+  k_scan_heads<<<(unsigned)nb, SCAN_THREADS, 0, s>>>(flags, n, part, starts, d_u);
+  IVF_LAUNCH_CHECK();
+  return cudaSuccess;
 }
 
 size_t radix_temp_bytes(int64_t n_max) {

@@ -18,6 +18,10 @@ namespace ivfk {
 size_t scan_temp_bytes(int64_t n);
 cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t s);
 cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* temp, cudaStream_t s);
+// n flags of 0 or 1 (run heads) -> starts[r] = position of the r-th head,
+// starts[U] = n, *d_u = U (starts must hold n + 1 values).
+cudaError_t heads_to_starts(const uint32_t* flags, int64_t n, uint32_t* starts, int64_t* d_u, void* temp,
+                            cudaStream_t s);
 
 // Stable LSD radix sort of d_n[0] (<= n_max) pairs, 8 bits per pass over the
 // low `bits` bits of the key.  Buffers ping-pong between (keys, vals) and

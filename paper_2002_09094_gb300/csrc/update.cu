@@ -118,8 +118,8 @@ __global__ void k_zc_keys(UpdateArgs a, uint32_t* keys, uint64_t* vals) {
   }
 }
 
-// Run heads of (cluster, term) in that order; after the scan,
-// scanned[e+1] != scanned[e] marks the first entry of a run.
+// Run heads of (cluster, term) in that order: flags[e] = 1 on the first
+// entry of a run (heads_to_starts turns them into the run starts).
 __global__ void k_zc_heads(const uint32_t* cl, const uint64_t* tv, const int64_t* d_n, uint32_t* flags) {
   const int64_t n = *d_n;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -719,9 +719,7 @@ cudaError_t launch_member_sums(const UpdateArgs& a, cudaStream_t s) {
   const uint64_t* tv = alt ? a.k64b : a.k64a;
   k_zc_heads<<<gE, T256, 0, s>>>(cl, tv, a.d_nnz, a.flags);
   IVF_LAUNCH_CHECK();
-  IVF_CU(exclusive_scan_u32(a.flags, a.flags, a.nnz, a.temp, s));
-  k_starts<<<gE, T256, 0, s>>>(a.flags, a.d_nnz, a.starts, a.d_u);
-  IVF_LAUNCH_CHECK();
+  IVF_CU(heads_to_starts(a.flags, a.nnz, a.starts, a.d_u, a.temp, s));
   k_zc_segsum<<<gE, T256, 0, s>>>(a, cl, tv);
   IVF_LAUNCH_CHECK();
   return cudaSuccess;
